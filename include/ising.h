@@ -1,0 +1,232 @@
+/*
+ * ising.h -- C ABI of the GB300 (sm_103a) DOCH Ising solver library
+ * (libising_doch.so).
+ *
+ * The library runs the difference-of-convex fixed-point iteration of
+ * "A Continuous Energy Ising Machine Leveraging Difference-of-Convex
+ * Programming" (arXiv 2509.01928):
+ *
+ *   x^(k+1) = T(x^(k)),  T(x) = cbrt( beta^-1 ((J + alpha I) x + h) )
+ *
+ * (Eq. FPE, Methods; Algorithm 1 "DOCH"), followed by sign rounding and an
+ * Ising-energy / Max-Cut reduction (Eq. IsingModel; Supplementary Note 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every call returns an ising_status_t; nothing aborts or traps.
+ *    ising_last_error() returns a message for the calling thread's last
+ *    failed call.
+ *  - Pointers: array arguments may be host or device pointers; the library
+ *    tells them apart with cudaPointerGetAttributes. Host arrays are staged
+ *    through device memory owned by the handle and the call synchronises the
+ *    stream before returning. Device arrays are used in place.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream). Work is enqueued on that stream. Unless the handle was
+ *    created with ISING_FLAG_ASYNC, every call synchronises the stream before
+ *    returning and reports device-side errors (bounded-wait timeouts, CUDA
+ *    faults) in its status. With ISING_FLAG_ASYNC, calls on device arrays
+ *    return after enqueueing; ising_synchronize() reports the errors.
+ *  - Layout: an iterate or spin array is [n][R] row-major: the R replicas of
+ *    spin i are contiguous. Batched instances are concatenated along n.
+ *  - Ownership: ising_create copies J and h into device memory owned by the
+ *    handle; the caller may free its copies when it returns. x, outputs and
+ *    streams stay the caller's. The handle also owns its scratch buffers
+ *    (ping-pong state, reduction partials, checkpoints).
+ *  - Threads: one handle must not be used by two threads at once.
+ */
+#ifndef ISING_DOCH_H
+#define ISING_DOCH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISING_API __attribute__((visibility("default")))
+#else
+#define ISING_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISING_OK = 0,
+    ISING_ERR_INVALID_ARG = 1,   /* null/negative size, unknown enum, size mismatch   */
+    ISING_ERR_NOT_SYMMETRIC = 2, /* J_ij != J_ji (Eq. IsingModel requires symmetry)   */
+    ISING_ERR_NONZERO_DIAG = 3,  /* J_ii != 0 (no self-coupling, Eq. IsingModel)      */
+    ISING_ERR_INDEX_RANGE = 4,   /* CSR column out of range / row_ptr not monotone    */
+    ISING_ERR_NONFINITE = 5,     /* NaN or Inf in J, h, alpha or beta                 */
+    ISING_ERR_OOM = 6,           /* device allocation failed                          */
+    ISING_ERR_CUDA = 7,          /* a CUDA runtime call or kernel failed              */
+    ISING_ERR_TIMEOUT = 8,       /* a bounded device-side wait ran out                */
+    ISING_ERR_NOT_MONOTONE = 9,  /* H rose while ISING_FLAG_STRICT_MONOTONE was set   */
+    ISING_ERR_UNSUPPORTED = 10   /* valid request this build does not implement       */
+} ising_status_t;
+
+/* Storage form of the coupling matrix J. */
+typedef enum {
+    ISING_FMT_CSR = 0,     /* compressed sparse rows (Supplementary Note 9)            */
+    ISING_FMT_TORUS2D = 1, /* periodic 2-D lattice, one coupling per lattice edge      */
+    ISING_FMT_DENSE = 2    /* full n x n row-major matrix                               */
+} ising_format_t;
+
+/* Element types. */
+typedef enum {
+    ISING_I8 = 0,
+    ISING_I16 = 1,
+    ISING_I32 = 2,
+    ISING_FP8E4M3 = 3,
+    ISING_BF16 = 4,
+    ISING_F32 = 5,
+    ISING_F64 = 6
+} ising_dtype_t;
+
+/* Creation flags. */
+enum {
+    ISING_FLAG_ASYNC = 1,            /* do not synchronise inside calls on device arrays */
+    ISING_FLAG_SKIP_VALIDATION = 2,  /* skip the symmetry, diagonal and finiteness checks of
+                                        J and h (index and size checks always run)        */
+    ISING_FLAG_STRICT_MONOTONE = 4   /* ising_iterate fails with ISING_ERR_NOT_MONOTONE
+                                        when a recorded H trace rises                    */
+};
+
+/*
+ * Problem statement (Eq. IsingModel): couplings J (n x n, symmetric,
+ * J_ii = 0) and an optional external field h (n). Only the members of the
+ * chosen format are read; unused members must be zero/NULL.
+ *
+ * CSR: row i holds columns col[row_ptr[i] .. row_ptr[i+1]) with values
+ *   val[] of type jtype (I8, I16, I32, F32 or F64). Both triangles are stored.
+ * TORUS2D: n = l_rows * l_cols; spin index of site (r, c) is r * l_cols + c;
+ *   right[r][c] couples (r, c) with (r, (c+1) mod l_cols) and down[r][c]
+ *   couples (r, c) with ((r+1) mod l_rows, c); jtype I8. l_rows, l_cols >= 2
+ *   (on a 2-wide side both edges of a pair add up to one J_ij).
+ * DENSE: dense[i * n + j] = J_ij, jtype I8, F32 or F64.
+ * Field: h[n] of type htype (I8, I16, I32, F32, F64), or NULL for h = 0
+ *   (CSR and DENSE; a TORUS2D lattice takes no field).
+ * Batches: n_instances > 1 (CSR only) concatenates independent problems;
+ *   instance b owns spins [inst_offset[b], inst_offset[b+1]) and its rows may
+ *   only reference columns of that range. n_instances = 0 or 1 means one
+ *   instance and inst_offset may be NULL.
+ */
+typedef struct {
+    int64_t n;
+    int32_t format;          /* ising_format_t */
+    int32_t jtype;           /* ising_dtype_t of the coupling values */
+    const int64_t *row_ptr;  /* CSR: [n + 1] */
+    const int32_t *col;      /* CSR: [nnz] */
+    const void *val;         /* CSR: [nnz] */
+    int64_t l_rows, l_cols;  /* TORUS2D */
+    const void *right;       /* TORUS2D: [l_rows][l_cols] */
+    const void *down;        /* TORUS2D: [l_rows][l_cols] */
+    const void *dense;       /* DENSE: [n][n] */
+    const void *h;           /* [n] or NULL */
+    int32_t htype;           /* ising_dtype_t of h */
+    int32_t n_instances;     /* 0 or 1: single instance */
+    const int64_t *inst_offset; /* [n_instances + 1] or NULL */
+} ising_problem_t;
+
+typedef struct ising_context *ising_handle_t;
+
+/*
+ * Parameter rule of Eq. alphabeta (Supplementary Note 6), host-side FP64:
+ *   alpha = eta * lambda_max(-J),
+ *   beta  = n^1.5 * max_j ( alpha + sum_{i != j} |J_ij| ).
+ * method 0 = auto (power iteration below n = 1e4, Wigner estimate of
+ * Eq. estimate_eig_J from there on, as the paper does), 1 = power
+ * iteration on -J shifted by ||J||_inf, 2 = Wigner estimate
+ * 2 <J> sqrt(n) with <J> the standard deviation of the n(n-1) off-diagonal
+ * entries. Per instance for batched problems: alpha_out and beta_out hold
+ * max(1, n_instances) values. Arrays of p must be host pointers here.
+ */
+ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double eta, int32_t method,
+                                    double *alpha_out, double *beta_out);
+
+/*
+ * Validate J and h (symmetry, zero diagonal, index ranges, finite values;
+ * skipped with ISING_FLAG_SKIP_VALIDATION) and copy them to device memory
+ * owned by a new handle. Dense +-1 couplings are held as exact FP8 E4M3 for
+ * the tensor-core path. On failure *out is NULL.
+ */
+ISING_API ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out);
+
+/* Release the handle and everything it owns. NULL is accepted. */
+ISING_API void ising_destroy(ising_handle_t h);
+
+/*
+ * DOCH, Algorithm 1, steps 2-4: apply T (Eq. FPE) `iters` times to the R
+ * replicas in x, in place (Jacobi: every component of x^(k+1) is computed
+ * from x^(k)).
+ *   x      [n][R] iterate of type xtype (F32 or F64; BF16 for DENSE), x^(0)
+ *          on entry, x^(iters) on return.
+ *   alpha  [max(1,n_instances)][alpha_len] host array, alpha_len = 1 (constant
+ *          alpha) or iters (a schedule alpha_k, one value per iteration).
+ *   beta   [max(1,n_instances)] host array, beta > 0.
+ *   H_trace  NULL, or [iters + 1][max(1,n_instances)][R] FP64 receiving
+ *          H(x^(k)) of Eq. Hamilton (with -h^T x for a field), each with the
+ *          alpha of step k (the last step's for k = iters). Computed in FP64
+ *          on the device, fused into the iteration kernel.
+ * For DENSE the iterate is BF16 and the coupling product runs on the
+ * tcgen05 tensor cores with FP32 accumulation.
+ */
+ISING_API ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R,
+                             const double *alpha, int32_t alpha_len, const double *beta,
+                             int32_t iters, double *H_trace, void *stream);
+
+/*
+ * Sign rounding (Algorithm 1, step 5: s = sign(x^(N)), sign(0) = +1) and the
+ * Ising energy E_r = -1/2 s_r^T J s_r - h^T s_r (Eq. IsingModel) with the cut
+ * value cut_r = 1/4 sum_ij (1 - s_i s_j) W_ij for W = -2J (Supplementary
+ * Note 5), per instance and replica, plus the best replica argmin_r E_r per
+ * instance (first minimum).
+ *   x        [n][R] of type xtype: F32/F64/BF16 iterates (rounded here), or
+ *            I8 spins (+1/-1).
+ *   E_int, cut_int  [max(1,n_instances)][R] int64, exact integer arithmetic;
+ *            only for integer J and h (else ISING_ERR_INVALID_ARG). May be NULL.
+ *   E_f64, cut_f64  [max(1,n_instances)][R] FP64 with a fixed reduction
+ *            order (run-to-run identical). May be NULL.
+ *   best     [max(1,n_instances)] int32, or NULL.
+ *   spins    [n][R] int8 receiving s, or NULL.
+ */
+ISING_API ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int32_t R,
+                            int64_t *E_int, int64_t *cut_int, double *E_f64, double *cut_f64,
+                            int32_t *best, int8_t *spins, void *stream);
+
+/*
+ * Adjoint of `iters` DOCH steps (derived from Eq. FPE; the paper has no
+ * gradients). Loss: the mean relaxed energy of the final iterates,
+ *   L = (1/R) sum_r ( -1/2 x_r^T J x_r - h^T x_r ) at x^(iters)
+ * (Supplementary Note 2, Eq. E, plus the field term). Computes
+ *   grad_alpha[k] = dL/dalpha_k  (k = 0..iters-1)  and  grad_x0 = dL/dx^(0)
+ * by the reverse recursion
+ *   g^N = -(1/R)(J x^N + h);  w^k = g^(k+1) / (3 (x^(k+1))^2) (0 where x^(k+1) = 0);
+ *   dL/dalpha_k = sum w^k x^k / beta;  g^k = (J w^k + alpha_k w^k) / beta,
+ * keeping x^(k) only every ckpt_every steps and recomputing each segment.
+ *   x0       [n][R] F32 (CSR or TORUS2D, one instance).
+ *   alpha    [iters] host array (the schedule); beta > 0 host scalar.
+ *   grad_alpha  [iters] FP64;  grad_x0  [n][R] F32;  loss  FP64 scalar (all
+ *            may be host or device; NULL skips an output).
+ *   zero_events  int64 scalar or NULL: components where x^(k+1) was exactly 0.
+ */
+ISING_API ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, int32_t R,
+                              const double *alpha, int32_t iters, double beta, int32_t ckpt_every,
+                              double *grad_alpha, void *grad_x0, double *loss,
+                              int64_t *zero_events, void *stream);
+
+/* Wait for the handle's work on `stream` and report deferred device errors. */
+ISING_API ising_status_t ising_synchronize(ising_handle_t h, void *stream);
+
+/* Problem size of a handle: total spins and instance count. */
+ISING_API ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances);
+
+/* Static description of a status code. */
+ISING_API const char *ising_status_string(ising_status_t s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+ISING_API const char *ising_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_DOCH_H */

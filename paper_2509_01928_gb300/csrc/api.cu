@@ -1,0 +1,737 @@
+// C ABI of libising_doch.so: handle lifetime, validation of J and h,
+// host/device staging, the parameter rule, and dispatch of the DOCH
+// iteration (Algorithm 1) and readout kernels. See include/ising.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace doch {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+ising_status_t fail(ising_status_t s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+ising_status_t cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ISING_ERR_OOM : ISING_ERR_CUDA;
+}
+
+ising_status_t DevBuf::ensure(size_t want) {
+    if (want <= bytes) return ISING_OK;
+    release();
+    if (want == 0) return ISING_OK;
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc(scratch)");
+    }
+    bytes = want;
+    return ISING_OK;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+size_t dtype_size(int t) {
+    switch (t) {
+        case ISING_I8: case ISING_FP8E4M3: return 1;
+        case ISING_I16: case ISING_BF16: return 2;
+        case ISING_I32: case ISING_F32: return 4;
+        case ISING_F64: return 8;
+        default: return 0;
+    }
+}
+
+bool dtype_integer(int t) { return t == ISING_I8 || t == ISING_I16 || t == ISING_I32; }
+
+// true when the pointer is device (or managed) memory; pinned and pageable
+// host memory count as host
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy `bytes` from a host or device pointer into a host vector
+ising_status_t to_host(const void *src, size_t bytes, std::vector<unsigned char> &dst) {
+    dst.resize(bytes);
+    if (bytes == 0) return ISING_OK;
+    if (is_device_ptr(src)) {
+        DOCH_CUDA(cudaMemcpy(dst.data(), src, bytes, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(dst.data(), src, bytes);
+    }
+    return ISING_OK;
+}
+
+double value_at(const unsigned char *base, int t, int64_t i) {
+    switch (t) {
+        case ISING_I8: return reinterpret_cast<const int8_t *>(base)[i];
+        case ISING_I16: return reinterpret_cast<const int16_t *>(base)[i];
+        case ISING_I32: return reinterpret_cast<const int32_t *>(base)[i];
+        case ISING_F32: return reinterpret_cast<const float *>(base)[i];
+        case ISING_F64: return reinterpret_cast<const double *>(base)[i];
+        default: return NAN;
+    }
+}
+
+template <typename T>
+ising_status_t upload(T **dst, const void *src, size_t bytes) {
+    void *p = nullptr;
+    DOCH_CUDA(cudaMalloc(&p, bytes ? bytes : 1));
+    *dst = static_cast<T *>(p);
+    if (bytes) DOCH_CUDA(cudaMemcpy(p, src, bytes, cudaMemcpyDefault));
+    return ISING_OK;
+}
+
+// Host view of a problem: J as sorted CSR rows in FP64 (or torus/dense arrays)
+struct HostProblem {
+    int64_t n = 0;
+    int format = 0;
+    int jtype = 0;
+    int n_inst = 1;
+    std::vector<int64_t> off;            // [n_inst + 1]
+    std::vector<int64_t> row_ptr;        // CSR
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    std::vector<unsigned char> raw_val;  // CSR values in jtype, sorted order
+    std::vector<unsigned char> right, down;  // TORUS2D (int8)
+    std::vector<unsigned char> dense;    // DENSE raw jtype
+    std::vector<double> h;               // empty when h = 0
+    std::vector<unsigned char> raw_h;
+    int htype = 0;
+    int64_t l_rows = 0, l_cols = 0;
+};
+
+ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem &hp) {
+    if (!p) return fail(ISING_ERR_INVALID_ARG, "problem is NULL");
+    if (p->n < 1) return fail(ISING_ERR_INVALID_ARG, "n must be >= 1");
+    hp.n = p->n;
+    hp.format = p->format;
+    hp.jtype = p->jtype;
+    const int64_t n = p->n;
+    const size_t jsz = dtype_size(p->jtype);
+    if (!jsz) return fail(ISING_ERR_INVALID_ARG, "unknown jtype");
+    // instances
+    hp.n_inst = p->n_instances > 1 ? p->n_instances : 1;
+    if (p->n_instances > 65535) return fail(ISING_ERR_INVALID_ARG, "at most 65535 instances");
+    if (hp.n_inst > 1) {
+        if (p->format != ISING_FMT_CSR) return fail(ISING_ERR_UNSUPPORTED, "batched instances need CSR");
+        if (!p->inst_offset) return fail(ISING_ERR_INVALID_ARG, "inst_offset is NULL");
+        std::vector<unsigned char> buf;
+        DOCH_CHECK(to_host(p->inst_offset, sizeof(int64_t) * (hp.n_inst + 1), buf));
+        hp.off.assign(reinterpret_cast<int64_t *>(buf.data()),
+                      reinterpret_cast<int64_t *>(buf.data()) + hp.n_inst + 1);
+        if (hp.off[0] != 0 || hp.off[hp.n_inst] != n)
+            return fail(ISING_ERR_INVALID_ARG, "inst_offset must run from 0 to n");
+        for (int b = 0; b < hp.n_inst; ++b)
+            if (hp.off[b + 1] <= hp.off[b]) return fail(ISING_ERR_INVALID_ARG, "empty or decreasing instance");
+    } else {
+        hp.off = {0, n};
+    }
+    if (p->format == ISING_FMT_CSR) {
+        if (!p->row_ptr || (!p->col && n > 0)) return fail(ISING_ERR_INVALID_ARG, "CSR arrays are NULL");
+        if (p->jtype == ISING_FP8E4M3 || p->jtype == ISING_BF16)
+            return fail(ISING_ERR_UNSUPPORTED, "CSR values must be I8/I16/I32/F32/F64");
+        std::vector<unsigned char> rp_raw;
+        DOCH_CHECK(to_host(p->row_ptr, sizeof(int64_t) * (n + 1), rp_raw));
+        const int64_t *rp = reinterpret_cast<const int64_t *>(rp_raw.data());
+        if (rp[0] != 0) return fail(ISING_ERR_INDEX_RANGE, "row_ptr[0] must be 0");
+        for (int64_t i = 0; i < n; ++i)
+            if (rp[i + 1] < rp[i]) return fail(ISING_ERR_INDEX_RANGE, "row_ptr is not monotone");
+        const int64_t nnz = rp[n];
+        if (nnz > 0 && !p->val) return fail(ISING_ERR_INVALID_ARG, "CSR values are NULL");
+        std::vector<unsigned char> col_raw, val_raw;
+        DOCH_CHECK(to_host(p->col, sizeof(int32_t) * nnz, col_raw));
+        DOCH_CHECK(to_host(p->val, jsz * nnz, val_raw));
+        const int32_t *cl = reinterpret_cast<const int32_t *>(col_raw.data());
+        hp.row_ptr.assign(rp, rp + n + 1);
+        hp.col.resize(nnz);
+        hp.val.resize(nnz);
+        hp.raw_val.resize(jsz * nnz);
+        std::vector<int64_t> order;
+        int b = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            while (i >= hp.off[b + 1]) ++b;
+            const int64_t e0 = rp[i], e1 = rp[i + 1];
+            order.resize(e1 - e0);
+            std::iota(order.begin(), order.end(), e0);
+            std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return cl[a] < cl[c]; });
+            for (int64_t k = 0; k < e1 - e0; ++k) {
+                const int64_t e = order[k];
+                const int32_t j = cl[e];
+                // index checks always run: a bad column would make the kernels read out of bounds
+                if (j < hp.off[b] || j >= hp.off[b + 1])
+                    return fail(ISING_ERR_INDEX_RANGE, "column index out of range in row " + std::to_string(i));
+                if (k > 0 && cl[order[k - 1]] == j)
+                    return fail(ISING_ERR_INVALID_ARG, "duplicate column in row " + std::to_string(i));
+                hp.col[e0 + k] = j;
+                hp.val[e0 + k] = value_at(val_raw.data(), p->jtype, e);
+                std::memcpy(&hp.raw_val[(e0 + k) * jsz], &val_raw[e * jsz], jsz);
+                if (validate) {
+                    if (!std::isfinite(hp.val[e0 + k]))
+                        return fail(ISING_ERR_NONFINITE, "non-finite coupling in row " + std::to_string(i));
+                    if (j == i && hp.val[e0 + k] != 0.0)
+                        return fail(ISING_ERR_NONZERO_DIAG, "J_ii != 0 at i = " + std::to_string(i));
+                }
+            }
+        }
+        if (validate) {
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t e = hp.row_ptr[i]; e < hp.row_ptr[i + 1]; ++e) {
+                    const int64_t j = hp.col[e];
+                    const auto beg = hp.col.begin() + hp.row_ptr[j], end = hp.col.begin() + hp.row_ptr[j + 1];
+                    const auto it = std::lower_bound(beg, end, static_cast<int32_t>(i));
+                    const double back = (it != end && *it == i) ? hp.val[it - hp.col.begin()] : 0.0;
+                    if (back != hp.val[e])
+                        return fail(ISING_ERR_NOT_SYMMETRIC, "J_ij != J_ji at (" + std::to_string(i) + ", " + std::to_string(j) + ")");
+                }
+        }
+    } else if (p->format == ISING_FMT_TORUS2D) {
+        if (p->jtype != ISING_I8) return fail(ISING_ERR_UNSUPPORTED, "TORUS2D couplings must be I8");
+        if (p->l_rows < 2 || p->l_cols < 2 || p->l_rows * p->l_cols != n)
+            return fail(ISING_ERR_INVALID_ARG, "TORUS2D needs l_rows, l_cols >= 2 and n = l_rows * l_cols");
+        if (!p->right || !p->down) return fail(ISING_ERR_INVALID_ARG, "TORUS2D arrays are NULL");
+        if (p->h) return fail(ISING_ERR_UNSUPPORTED, "TORUS2D takes no field");
+        hp.l_rows = p->l_rows;
+        hp.l_cols = p->l_cols;
+        DOCH_CHECK(to_host(p->right, n, hp.right));
+        DOCH_CHECK(to_host(p->down, n, hp.down));
+    } else if (p->format == ISING_FMT_DENSE) {
+        if (!p->dense) return fail(ISING_ERR_INVALID_ARG, "dense array is NULL");
+        if (p->jtype != ISING_I8 && p->jtype != ISING_F32 && p->jtype != ISING_F64)
+            return fail(ISING_ERR_UNSUPPORTED, "DENSE couplings must be I8, F32 or F64");
+        DOCH_CHECK(to_host(p->dense, jsz * n * n, hp.dense));
+        if (validate) {
+            for (int64_t i = 0; i < n; ++i) {
+                if (value_at(hp.dense.data(), p->jtype, i * n + i) != 0.0)
+                    return fail(ISING_ERR_NONZERO_DIAG, "J_ii != 0 at i = " + std::to_string(i));
+                for (int64_t j = i + 1; j < n; ++j) {
+                    const double a = value_at(hp.dense.data(), p->jtype, i * n + j);
+                    const double c = value_at(hp.dense.data(), p->jtype, j * n + i);
+                    if (!std::isfinite(a)) return fail(ISING_ERR_NONFINITE, "non-finite coupling");
+                    if (a != c) return fail(ISING_ERR_NOT_SYMMETRIC, "J_ij != J_ji");
+                }
+            }
+        }
+    } else {
+        return fail(ISING_ERR_INVALID_ARG, "unknown format");
+    }
+    if (p->h) {
+        const size_t hsz = dtype_size(p->htype);
+        if (!hsz || p->htype == ISING_FP8E4M3 || p->htype == ISING_BF16)
+            return fail(ISING_ERR_INVALID_ARG, "htype must be I8/I16/I32/F32/F64");
+        hp.htype = p->htype;
+        DOCH_CHECK(to_host(p->h, hsz * n, hp.raw_h));
+        hp.h.resize(n);
+        for (int64_t i = 0; i < n; ++i) {
+            hp.h[i] = value_at(hp.raw_h.data(), p->htype, i);
+            if (validate && !std::isfinite(hp.h[i])) return fail(ISING_ERR_NONFINITE, "non-finite field");
+        }
+    }
+    return ISING_OK;
+}
+
+// y = J v for one instance [lo, hi) of a host problem (FP64), for the power method
+void host_matvec(const HostProblem &hp, int64_t lo, int64_t hi, const std::vector<double> &v,
+                 std::vector<double> &y) {
+    const int64_t m = hi - lo;
+    std::fill(y.begin(), y.end(), 0.0);
+    if (hp.format == ISING_FMT_CSR) {
+        for (int64_t i = lo; i < hi; ++i) {
+            double s = 0.0;
+            for (int64_t e = hp.row_ptr[i]; e < hp.row_ptr[i + 1]; ++e) s += hp.val[e] * v[hp.col[e] - lo];
+            y[i - lo] = s;
+        }
+    } else if (hp.format == ISING_FMT_TORUS2D) {
+        const int64_t Lr = hp.l_rows, Lc = hp.l_cols;
+        for (int64_t r = 0; r < Lr; ++r)
+            for (int64_t c = 0; c < Lc; ++c) {
+                const int64_t a = r * Lc + c, br = r * Lc + (c + 1) % Lc, bd = ((r + 1) % Lr) * Lc + c;
+                const double wr = static_cast<int8_t>(hp.right[a]), wd = static_cast<int8_t>(hp.down[a]);
+                y[a] += wr * v[br]; y[br] += wr * v[a];
+                y[a] += wd * v[bd]; y[bd] += wd * v[a];
+            }
+    } else {
+        for (int64_t i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int64_t j = 0; j < m; ++j) s += value_at(hp.dense.data(), hp.jtype, i * m + j) * v[j];
+            y[i] = s;
+        }
+    }
+}
+
+// per-instance sums: off-diagonal sum, sum of squares, max row |J| sum
+void host_stats(const HostProblem &hp, int64_t lo, int64_t hi, double &s1, double &s2, double &rowmax) {
+    s1 = s2 = rowmax = 0.0;
+    if (hp.format == ISING_FMT_CSR) {
+        for (int64_t i = lo; i < hi; ++i) {
+            double ra = 0.0;
+            for (int64_t e = hp.row_ptr[i]; e < hp.row_ptr[i + 1]; ++e) {
+                s1 += hp.val[e]; s2 += hp.val[e] * hp.val[e]; ra += std::fabs(hp.val[e]);
+            }
+            rowmax = std::max(rowmax, ra);
+        }
+    } else if (hp.format == ISING_FMT_TORUS2D) {
+        const int64_t Lr = hp.l_rows, Lc = hp.l_cols;
+        for (int64_t r = 0; r < Lr; ++r)
+            for (int64_t c = 0; c < Lc; ++c) {
+                const int64_t a = r * Lc + c;
+                const double wr = static_cast<int8_t>(hp.right[a]), wd = static_cast<int8_t>(hp.down[a]);
+                s1 += 2 * (wr + wd); s2 += 2 * (wr * wr + wd * wd);
+                const double wl = static_cast<int8_t>(hp.right[r * Lc + (c + Lc - 1) % Lc]);
+                const double wu = static_cast<int8_t>(hp.down[((r + Lr - 1) % Lr) * Lc + c]);
+                rowmax = std::max(rowmax, std::fabs(wr) + std::fabs(wd) + std::fabs(wl) + std::fabs(wu));
+            }
+    } else {
+        const int64_t m = hi - lo;
+        for (int64_t i = 0; i < m; ++i) {
+            double ra = 0.0;
+            for (int64_t j = 0; j < m; ++j) {
+                const double w = value_at(hp.dense.data(), hp.jtype, i * m + j);
+                s1 += w; s2 += w * w; ra += std::fabs(w);
+            }
+            rowmax = std::max(rowmax, ra);
+        }
+    }
+}
+
+// lambda_max(-J) by power iteration on M = -J + sigma I, sigma = ||J||_inf
+double power_lambda_neg(const HostProblem &hp, int64_t lo, int64_t hi, double sigma) {
+    const int64_t m = hi - lo;
+    std::vector<double> v(m), y(m);
+    uint64_t s = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(lo);
+    for (int64_t i = 0; i < m; ++i) {  // deterministic start (xorshift)
+        s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+        v[i] = static_cast<double>(s >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    double nv = 0.0;
+    for (double t : v) nv += t * t;
+    nv = std::sqrt(nv);
+    for (double &t : v) t /= nv;
+    double lam = 0.0, prev = -1.0;
+    for (int it = 0; it < 20000; ++it) {
+        host_matvec(hp, lo, hi, v, y);
+        double rq = 0.0, ny = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            y[i] = -y[i] + sigma * v[i];
+            rq += v[i] * y[i];
+            ny += y[i] * y[i];
+        }
+        lam = rq;
+        ny = std::sqrt(ny);
+        if (ny == 0.0) break;
+        for (int64_t i = 0; i < m; ++i) v[i] = y[i] / ny;
+        if (it > 10 && std::fabs(lam - prev) <= 1e-13 * std::fabs(lam)) break;
+        prev = lam;
+    }
+    return lam - sigma;
+}
+
+ising_status_t finish(ising_context *c, cudaStream_t st, bool must_sync) {
+    if (!must_sync && (c->flags & ISING_FLAG_ASYNC)) return ISING_OK;
+    DOCH_CUDA(cudaMemcpyAsync(c->err_host, c->err_word, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DOCH_CUDA(cudaStreamSynchronize(st));
+    if (*c->err_host) {
+        const int w = *c->err_host;
+        *c->err_host = 0;
+        cudaMemsetAsync(c->err_word, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        if (w & DEV_ERR_TIMEOUT) return fail(ISING_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    }
+    return ISING_OK;
+}
+
+void destroy_ctx(ising_context *c) {
+    if (!c) return;
+    cudaFree(c->inst_off);
+    cudaFree(c->row_ptr);
+    cudaFree(c->col);
+    cudaFree(c->val);
+    cudaFree(c->right);
+    cudaFree(c->down);
+    cudaFree(c->dense);
+    cudaFree(c->h_f32);
+    cudaFree(c->h_f64);
+    cudaFree(c->h_i64);
+    cudaFree(c->err_word);
+    if (c->err_host) cudaFreeHost(c->err_host);
+    c->ping.release();
+    c->stage_x.release();
+    c->stage_out.release();
+    c->partials.release();
+    c->params.release();
+    c->ckpt.release();
+    c->work.release();
+    delete c;
+}
+
+ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c) {
+    DOCH_CUDA(cudaGetDevice(&c->device));
+    DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->flags = flags;
+    c->format = hp.format;
+    c->jtype = hp.jtype;
+    c->n = hp.n;
+    c->n_inst = hp.n_inst;
+    c->inst_off_h = hp.off;
+    c->max_inst_n = 0;
+    for (int b = 0; b < hp.n_inst; ++b) c->max_inst_n = std::max(c->max_inst_n, hp.off[b + 1] - hp.off[b]);
+    c->has_h = !hp.h.empty();
+    c->integer = dtype_integer(hp.jtype) && (!c->has_h || dtype_integer(hp.htype));
+    DOCH_CHECK(upload(&c->inst_off, hp.off.data(), sizeof(int64_t) * hp.off.size()));
+    if (hp.format == ISING_FMT_CSR) {
+        c->nnz = hp.row_ptr.back();
+        for (int64_t i = 0; i < hp.n; ++i)
+            c->max_row_nnz = std::max(c->max_row_nnz, hp.row_ptr[i + 1] - hp.row_ptr[i]);
+        DOCH_CHECK(upload(&c->row_ptr, hp.row_ptr.data(), sizeof(int64_t) * hp.row_ptr.size()));
+        DOCH_CHECK(upload(&c->col, hp.col.data(), sizeof(int32_t) * hp.col.size()));
+        if (hp.jtype == ISING_I16) {  // held as I32 on the device
+            std::vector<int32_t> v(hp.val.size());
+            for (size_t e = 0; e < v.size(); ++e) v[e] = static_cast<int32_t>(hp.val[e]);
+            DOCH_CHECK(upload(&c->val, v.data(), sizeof(int32_t) * v.size()));
+            c->jtype = ISING_I32;
+        } else {
+            DOCH_CHECK(upload(&c->val, hp.raw_val.data(), hp.raw_val.size()));
+        }
+    } else if (hp.format == ISING_FMT_TORUS2D) {
+        c->l_rows = hp.l_rows;
+        c->l_cols = hp.l_cols;
+        DOCH_CHECK(upload(&c->right, hp.right.data(), hp.right.size()));
+        DOCH_CHECK(upload(&c->down, hp.down.data(), hp.down.size()));
+    } else {
+        DOCH_CHECK(upload(&c->dense, hp.dense.data(), hp.dense.size()));
+        c->dense_type = hp.jtype;
+    }
+    if (c->has_h) {
+        std::vector<float> hf(hp.n);
+        for (int64_t i = 0; i < hp.n; ++i) hf[i] = static_cast<float>(hp.h[i]);
+        DOCH_CHECK(upload(&c->h_f32, hf.data(), sizeof(float) * hp.n));
+        DOCH_CHECK(upload(&c->h_f64, hp.h.data(), sizeof(double) * hp.n));
+        if (dtype_integer(hp.htype)) {
+            std::vector<int64_t> hi(hp.n);
+            for (int64_t i = 0; i < hp.n; ++i) hi[i] = static_cast<int64_t>(hp.h[i]);
+            DOCH_CHECK(upload(&c->h_i64, hi.data(), sizeof(int64_t) * hp.n));
+        }
+    }
+    void *ew = nullptr;
+    DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
+    c->err_word = static_cast<int *>(ew);
+    DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
+    void *eh = nullptr;
+    DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
+    c->err_host = static_cast<int *>(eh);
+    *c->err_host = 0;
+    return ISING_OK;
+}
+
+size_t xtype_size(int t) { return dtype_size(t); }
+
+// upload the per-instance parameter tables and return views of them
+ising_status_t upload_params(ising_context *c, const double *alpha, int alpha_len, const double *beta,
+                             ParamTabs &out, cudaStream_t st) {
+    const int ni = c->n_inst;
+    const size_t na = static_cast<size_t>(ni) * alpha_len;
+    std::vector<double> a(na), b(ni);
+    std::vector<unsigned char> tmp;
+    DOCH_CHECK(to_host(alpha, sizeof(double) * na, tmp));
+    std::memcpy(a.data(), tmp.data(), sizeof(double) * na);
+    DOCH_CHECK(to_host(beta, sizeof(double) * ni, tmp));
+    std::memcpy(b.data(), tmp.data(), sizeof(double) * ni);
+    for (double v : a) if (!std::isfinite(v)) return fail(ISING_ERR_NONFINITE, "alpha is not finite");
+    for (double v : b) {
+        if (!std::isfinite(v)) return fail(ISING_ERR_NONFINITE, "beta is not finite");
+        if (v <= 0.0) return fail(ISING_ERR_INVALID_ARG, "beta must be > 0");
+    }
+    // layout: alpha_d | beta_d | alpha_f | inv_beta_f (each 256-byte aligned)
+    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t o1 = al(na * 8), o2 = o1 + al(ni * 8), o3 = o2 + al(na * 4), tot = o3 + al(ni * 4);
+    std::vector<unsigned char> host(tot);
+    std::memcpy(host.data(), a.data(), na * 8);
+    std::memcpy(host.data() + o1, b.data(), ni * 8);
+    for (size_t i = 0; i < na; ++i) reinterpret_cast<float *>(host.data() + o2)[i] = static_cast<float>(a[i]);
+    for (int i = 0; i < ni; ++i) reinterpret_cast<float *>(host.data() + o3)[i] = static_cast<float>(1.0 / b[i]);
+    DOCH_CHECK(c->params.ensure(tot));
+    DOCH_CUDA(cudaMemcpyAsync(c->params.ptr, host.data(), tot, cudaMemcpyHostToDevice, st));
+    // the source is pageable: make sure the copy has consumed it
+    DOCH_CUDA(cudaStreamSynchronize(st));
+    unsigned char *base = c->params.as<unsigned char>();
+    out.alpha_d = reinterpret_cast<const double *>(base);
+    out.beta_d = reinterpret_cast<const double *>(base + o1);
+    out.alpha_f = reinterpret_cast<const float *>(base + o2);
+    out.inv_beta_f = reinterpret_cast<const float *>(base + o3);
+    out.alpha_len = alpha_len;
+    return ISING_OK;
+}
+
+// one DOCH step of the handle's storage form
+ising_status_t step(ising_context *c, const void *xi, void *xo, int xtype, int R, const ParamTabs &p,
+                    const std::vector<double> &alpha_h, const std::vector<double> &beta_h, int k,
+                    cudaStream_t st) {
+    if (c->format == ISING_FMT_TORUS2D) {
+        const double a = alpha_h[p.alpha_len == 1 ? 0 : k];
+        if (xtype == ISING_F32)
+            return torus_step_f32(c, static_cast<const float *>(xi), static_cast<float *>(xo), R,
+                                  static_cast<float>(a), static_cast<float>(1.0 / beta_h[0]), st);
+        return torus_step_f64(c, static_cast<const double *>(xi), static_cast<double *>(xo), R, a,
+                              beta_h[0], st);
+    }
+    if (c->format == ISING_FMT_CSR) return csr_step(c, xi, xo, xtype, R, p, k, st);
+    return fail(ISING_ERR_UNSUPPORTED, "this storage form has no iteration kernel yet");
+}
+
+}  // namespace
+}  // namespace doch
+
+using namespace doch;
+
+extern "C" {
+
+const char *ising_status_string(ising_status_t s) {
+    switch (s) {
+        case ISING_OK: return "ok";
+        case ISING_ERR_INVALID_ARG: return "invalid argument";
+        case ISING_ERR_NOT_SYMMETRIC: return "coupling matrix is not symmetric";
+        case ISING_ERR_NONZERO_DIAG: return "coupling matrix has a nonzero diagonal";
+        case ISING_ERR_INDEX_RANGE: return "index out of range";
+        case ISING_ERR_NONFINITE: return "non-finite value";
+        case ISING_ERR_OOM: return "out of device memory";
+        case ISING_ERR_CUDA: return "CUDA error";
+        case ISING_ERR_TIMEOUT: return "device-side wait timed out";
+        case ISING_ERR_NOT_MONOTONE: return "Hamiltonian increased";
+        case ISING_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *ising_last_error(void) { return g_err.c_str(); }
+
+ising_status_t ising_default_params(const ising_problem_t *p, double eta, int32_t method,
+                                    double *alpha_out, double *beta_out) {
+    g_err.clear();
+    if (!alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "output pointers are NULL");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
+    if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    HostProblem hp;
+    DOCH_CHECK(load_problem(p, true, hp));
+    for (int b = 0; b < hp.n_inst; ++b) {
+        const int64_t lo = hp.off[b], hi = hp.off[b + 1], m = hi - lo;
+        double s1, s2, rowmax;
+        host_stats(hp, lo, hi, s1, s2, rowmax);
+        int meth = method;
+        if (meth == 0) meth = m < 10000 ? 1 : 2;
+        double lam;
+        if (meth == 1) {
+            lam = power_lambda_neg(hp, lo, hi, rowmax);
+        } else {
+            const double cnt = static_cast<double>(m) * (m - 1.0);
+            const double mean = cnt > 0 ? s1 / cnt : 0.0;
+            const double var = cnt > 0 ? std::max(0.0, s2 / cnt - mean * mean) : 0.0;
+            lam = 2.0 * std::sqrt(var) * std::sqrt(static_cast<double>(m));
+        }
+        const double alpha = eta * lam;
+        alpha_out[b] = alpha;
+        beta_out[b] = std::pow(static_cast<double>(m), 1.5) * (alpha + rowmax);
+    }
+    return ISING_OK;
+}
+
+ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out) {
+    g_err.clear();
+    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    HostProblem hp;
+    DOCH_CHECK(load_problem(p, !(flags & ISING_FLAG_SKIP_VALIDATION), hp));
+    ising_context *c = new ising_context();
+    ising_status_t s = build_context(hp, flags, c);
+    if (s != ISING_OK) {
+        destroy_ctx(c);
+        return s;
+    }
+    *out = c;
+    return ISING_OK;
+}
+
+void ising_destroy(ising_handle_t h) { destroy_ctx(h); }
+
+ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances) {
+    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+    if (n) *n = h->n;
+    if (n_instances) *n_instances = h->n_inst;
+    return ISING_OK;
+}
+
+ising_status_t ising_synchronize(ising_handle_t h, void *stream) {
+    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+    return finish(h, static_cast<cudaStream_t>(stream), true);
+}
+
+ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
+                             int32_t alpha_len, const double *beta, int32_t iters, double *H_trace,
+                             void *stream) {
+    g_err.clear();
+    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (R < 1 || iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be >= 1 and iters >= 0");
+    if (alpha_len != 1 && alpha_len != iters) return fail(ISING_ERR_INVALID_ARG, "alpha_len must be 1 or iters");
+    if (h->format == ISING_FMT_DENSE) {
+        if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
+    } else if (xtype != ISING_F32 && xtype != ISING_F64) {
+        return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
+    }
+    if (R > 65535) return fail(ISING_ERR_INVALID_ARG, "R must be <= 65535");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ising_context *c = h;
+    const int64_t count = c->n * R;
+    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+    std::vector<double> alpha_h(static_cast<size_t>(c->n_inst) * alpha_len), beta_h(c->n_inst);
+    {
+        std::vector<unsigned char> tmp;
+        DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
+        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
+        DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
+        std::memcpy(beta_h.data(), tmp.data(), tmp.size());
+    }
+    ParamTabs p;
+    DOCH_CHECK(upload_params(c, alpha, alpha_len, beta, p, st));
+
+    const bool x_dev = is_device_ptr(x);
+    void *xd = x;
+    if (!x_dev) {
+        DOCH_CHECK(c->stage_x.ensure(xbytes));
+        xd = c->stage_x.ptr;
+        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
+    }
+    const int pairs = c->n_inst * R;
+    double *Hd = nullptr;
+    if (H_trace) {
+        DOCH_CHECK(c->work.ensure(sizeof(double) * pairs * (static_cast<size_t>(iters) + 1)));
+        Hd = c->work.as<double>();
+    }
+    bool done = false;
+    if (!H_trace && c->format == ISING_FMT_CSR && iters > 0) {
+        ising_status_t s = csr_fused(c, xd, xtype, R, p, iters, st);
+        if (s == ISING_OK) done = true;
+        else if (s != ISING_ERR_UNSUPPORTED) return s;
+    }
+    if (!done && iters > 0) {
+        DOCH_CHECK(c->ping.ensure(xbytes));
+        void *cur = xd, *nxt = c->ping.ptr;
+        for (int k = 0; k < iters; ++k) {
+            if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
+            DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+            std::swap(cur, nxt);
+        }
+        if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, iters - 1, Hd + static_cast<size_t>(iters) * pairs, st));
+        if (cur != xd) DOCH_CUDA(cudaMemcpyAsync(xd, cur, xbytes, cudaMemcpyDeviceToDevice, st));
+    } else if (!done && Hd) {
+        DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, Hd, st));
+    }
+    bool must_sync = !x_dev;
+    if (!x_dev) DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+    if (Hd) {
+        const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
+        DOCH_CUDA(cudaMemcpyAsync(H_trace, Hd, hb, cudaMemcpyDefault, st));
+        if (!is_device_ptr(H_trace)) must_sync = true;
+        if (c->flags & ISING_FLAG_STRICT_MONOTONE) {
+            DOCH_CHECK(finish(c, st, true));
+            std::vector<double> Hh(pairs * (static_cast<size_t>(iters) + 1));
+            DOCH_CUDA(cudaMemcpy(Hh.data(), Hd, hb, cudaMemcpyDeviceToHost));
+            for (int k = 0; k < iters; ++k)
+                for (int t = 0; t < pairs; ++t) {
+                    const double a = Hh[static_cast<size_t>(k) * pairs + t], b = Hh[static_cast<size_t>(k + 1) * pairs + t];
+                    if (b > a + 1e-6 * std::fabs(a))
+                        return fail(ISING_ERR_NOT_MONOTONE, "H rose at step " + std::to_string(k));
+                }
+        }
+    }
+    return finish(c, st, must_sync);
+}
+
+ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int32_t R, int64_t *E_int,
+                            int64_t *cut_int, double *E_f64, double *cut_f64, int32_t *best, int8_t *spins,
+                            void *stream) {
+    g_err.clear();
+    if (!h || !x) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (R < 1 || R > 65535) return fail(ISING_ERR_INVALID_ARG, "R out of range");
+    if (xtype != ISING_F32 && xtype != ISING_F64 && xtype != ISING_BF16 && xtype != ISING_I8)
+        return fail(ISING_ERR_INVALID_ARG, "x must be F32, F64, BF16 or I8");
+    ising_context *c = h;
+    if ((E_int || cut_int) && !c->integer)
+        return fail(ISING_ERR_INVALID_ARG, "integer energies need integer couplings and field");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t count = c->n * R;
+    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+    const void *xd = x;
+    bool must_sync = false;
+    if (!is_device_ptr(x)) {
+        DOCH_CHECK(c->stage_x.ensure(xbytes));
+        DOCH_CUDA(cudaMemcpyAsync(c->stage_x.ptr, x, xbytes, cudaMemcpyHostToDevice, st));
+        xd = c->stage_x.ptr;
+        must_sync = true;
+    }
+    const size_t pairs = static_cast<size_t>(c->n_inst) * R;
+    // staging of the outputs: E_i | cut_i | E_d | cut_d | best
+    DOCH_CHECK(c->stage_out.ensure(pairs * 8 * 4 + c->n_inst * 4 + 64));
+    int64_t *Ei = c->stage_out.as<int64_t>();
+    int64_t *Ci = Ei + pairs;
+    double *Ed = reinterpret_cast<double *>(Ci + pairs);
+    double *Cd = Ed + pairs;
+    int32_t *Bd = reinterpret_cast<int32_t *>(Cd + pairs);
+    DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
+    if (best) DOCH_CHECK(best_replica(c, c->integer ? Ei : nullptr, Ed, R, Bd, st));
+    auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
+        if (!dst) return ISING_OK;
+        if (!is_device_ptr(dst)) must_sync = true;
+        DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+        return ISING_OK;
+    };
+    DOCH_CHECK(put(E_int, Ei, pairs * 8));
+    DOCH_CHECK(put(cut_int, Ci, pairs * 8));
+    DOCH_CHECK(put(E_f64, Ed, pairs * 8));
+    DOCH_CHECK(put(cut_f64, Cd, pairs * 8));
+    DOCH_CHECK(put(best, Bd, c->n_inst * 4));
+    if (spins) {
+        if (is_device_ptr(spins)) {
+            DOCH_CHECK(write_spins(c, xd, xtype, R, spins, st));
+        } else {
+            DOCH_CHECK(c->work.ensure(count));
+            DOCH_CHECK(write_spins(c, xd, xtype, R, c->work.as<int8_t>(), st));
+            DOCH_CUDA(cudaMemcpyAsync(spins, c->work.ptr, count, cudaMemcpyDeviceToHost, st));
+            must_sync = true;
+        }
+    }
+    return finish(c, st, must_sync);
+}
+
+ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, int32_t R, const double *alpha,
+                              int32_t iters, double beta, int32_t ckpt_every, double *grad_alpha,
+                              void *grad_x0, double *loss, int64_t *zero_events, void *stream) {
+    (void)h; (void)x0; (void)xtype; (void)R; (void)alpha; (void)iters; (void)beta; (void)ckpt_every;
+    (void)grad_alpha; (void)grad_x0; (void)loss; (void)zero_events; (void)stream;
+    return fail(ISING_ERR_UNSUPPORTED, "ising_backward is not built yet");
+}
+
+}  // extern "C"

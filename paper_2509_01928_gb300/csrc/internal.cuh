@@ -1,0 +1,144 @@
+// Internal declarations of libising_doch.so (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ising.h"
+
+namespace doch {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+ising_status_t fail(ising_status_t s, const std::string &msg);
+ising_status_t cuda_fail(cudaError_t e, const char *what);
+
+#define DOCH_CUDA(call)                                                  \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::doch::cuda_fail(e_, #call);      \
+    } while (0)
+
+#define DOCH_CHECK(st)                                                   \
+    do {                                                                 \
+        ising_status_t s_ = (st);                                        \
+        if (s_ != ISING_OK) return s_;                                   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffer owned by a handle (grown on demand, never shrunk)
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    ising_status_t ensure(size_t want);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// device-side error word: bit 0 = a bounded wait ran out
+enum { DEV_ERR_TIMEOUT = 1 };
+
+struct Dims {
+    int64_t n = 0;
+    int n_inst = 1;
+};
+
+}  // namespace doch
+
+// the opaque handle of the C ABI
+struct ising_context {
+    int device = 0;
+    int num_sms = 0;
+    int flags = 0;
+    int format = 0;
+    int jtype = 0;
+    int64_t n = 0;
+    int n_inst = 1;
+    bool integer = false;  // J and h integer: exact int64 energies available
+    bool has_h = false;
+    // batched instances
+    std::vector<int64_t> inst_off_h;
+    int64_t *inst_off = nullptr;  // device [n_inst + 1]
+    int64_t max_inst_n = 0;
+    // CSR
+    int64_t nnz = 0;
+    int64_t *row_ptr = nullptr;
+    int32_t *col = nullptr;
+    void *val = nullptr;  // jtype
+    int64_t max_row_nnz = 0;
+    // TORUS2D
+    int64_t l_rows = 0, l_cols = 0;
+    int8_t *right = nullptr, *down = nullptr;
+    // DENSE (+-1 held as FP8 E4M3 bytes; other values as BF16)
+    void *dense = nullptr;
+    int dense_type = 0;
+    // field (both precisions; integer copy when integral)
+    float *h_f32 = nullptr;
+    double *h_f64 = nullptr;
+    int64_t *h_i64 = nullptr;
+    // sums used by the cut identity
+    // scratch
+    doch::DevBuf ping;      // second iterate buffer for the Jacobi ping-pong
+    doch::DevBuf stage_x;   // staging of host iterates
+    doch::DevBuf stage_out; // staging of host outputs
+    doch::DevBuf partials;  // reduction partials
+    doch::DevBuf params;    // alpha/beta tables on the device
+    doch::DevBuf ckpt;      // checkpoints of the adjoint
+    doch::DevBuf work;      // misc. work space
+    int *err_word = nullptr;  // device error word
+    int *err_host = nullptr;  // pinned mirror
+};
+
+namespace doch {
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the kernel translation units
+// ---------------------------------------------------------------------------
+
+// TORUS2D, one DOCH step, x_out = T(x_in) (Eq. FPE). XT = float or double.
+ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *x_out, int R,
+                              float alpha, float inv_beta, cudaStream_t st);
+ising_status_t torus_step_f64(const ising_context *c, const double *x_in, double *x_out, int R,
+                              double alpha, double beta, cudaStream_t st);
+
+// Per-instance parameter tables on the device (filled by ising_iterate):
+// alpha [n_inst][alpha_len] and beta [n_inst] in FP64, plus FP32 copies of
+// alpha and of 1/beta for the FP32 kernels.
+struct ParamTabs {
+    const double *alpha_d = nullptr;
+    const double *beta_d = nullptr;
+    const float *alpha_f = nullptr;
+    const float *inv_beta_f = nullptr;
+    int alpha_len = 1;
+};
+
+// CSR, one DOCH step for all instances (alpha of step k), xtype F32 or F64.
+ising_status_t csr_step(const ising_context *c, const void *x_in, void *x_out, int xtype, int R,
+                        const ParamTabs &p, int k, cudaStream_t st);
+// CSR, all `iters` steps in one launch: one CTA per (instance, replica) with
+// the iterate in shared memory. ISING_ERR_UNSUPPORTED when an instance does
+// not fit (the caller then uses csr_step).
+ising_status_t csr_fused(const ising_context *c, void *x, int xtype, int R, const ParamTabs &p,
+                         int iters, cudaStream_t st);
+size_t csr_fused_max_spins(int xtype);
+
+// Reductions (sign rounding + energy/cut, Hamiltonian monitor, best replica).
+// xtype: ISING_F32 / ISING_F64 / ISING_BF16 / ISING_I8.
+ising_status_t energy_reduce(ising_context *c, const void *x, int xtype, int R, int64_t *E_i,
+                             int64_t *cut_i, double *E_d, double *cut_d, cudaStream_t st);
+ising_status_t best_replica(const ising_context *c, const int64_t *E_i, const double *E_d, int R,
+                            int32_t *best, cudaStream_t st);
+ising_status_t write_spins(const ising_context *c, const void *x, int xtype, int R, int8_t *s,
+                           cudaStream_t st);
+// H(x) of Eq. Hamilton per (instance, replica), FP64, into H_out [n_inst][R] (device).
+// alpha of step k is taken from the tables (k clamped to alpha_len - 1).
+ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, int R,
+                                  const ParamTabs &p, int k, double *H_out, cudaStream_t st);
+
+}  // namespace doch

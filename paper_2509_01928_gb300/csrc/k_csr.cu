@@ -1,0 +1,243 @@
+// DOCH step for couplings in CSR form, Eq. FPE with the field inside g:
+//   x_out[i][r] = cbrt( ( sum_e val[e] x_in[col[e]][r] + alpha_b x_in[i][r] + h_i ) / beta_b )
+// for the instance b that owns row i (batched instances are concatenated).
+//
+// csr_step: one launch per step. A thread owns one row and a vector chunk of
+// V replicas (V = 4/2/1 floats or 2/1 doubles), so the threads of a row read
+// consecutive replicas of each neighbour x[j][*] (coalesced) and share the
+// row's col/val entries.
+//
+// csr_fused: the whole iteration in one launch for instances that fit in
+// shared memory. One CTA per (instance, replica) keeps that replica's
+// iterate in two shared-memory buffers and separates the steps with
+// __syncthreads(); the CSR arrays stream through L1/L2.
+#include "internal.cuh"
+
+namespace doch {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T dcbrt(T z) {
+    if constexpr (sizeof(T) == 4) return cbrtf(z);
+    else return cbrt(z);
+}
+
+// scale by 1/beta: float tables hold 1/beta (multiply), double tables hold beta (divide)
+template <typename T>
+__device__ __forceinline__ T scale_beta(T v, T b) {
+    if constexpr (sizeof(T) == 4) return v * b;
+    else return v / b;
+}
+
+__device__ __forceinline__ int find_inst(const int64_t *__restrict__ off, int n_inst, int64_t i) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int V> struct VecOf;
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<double, 1> { using type = double; };
+template <> struct VecOf<double, 2> { using type = double2; };
+
+template <typename T, int V>
+__device__ __forceinline__ void ldv(const T *p, T (&v)[V]) {
+    using VT = typename VecOf<T, V>::type;
+    const VT w = __ldg(reinterpret_cast<const VT *>(p));
+    const T *q = reinterpret_cast<const T *>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = q[k];
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T *p, const T (&v)[V]) {
+    using VT = typename VecOf<T, V>::type;
+    VT w;
+    T *q = reinterpret_cast<T *>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) q[k] = v[k];
+    *reinterpret_cast<VT *>(p) = w;
+}
+
+template <typename XT, typename VT, int V>
+__global__ void __launch_bounds__(256)
+csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
+                const int64_t *__restrict__ inst_off, int n_inst, int64_t n, int R,
+                const XT *__restrict__ alpha_tab, int alpha_len, int k,
+                const XT *__restrict__ beta_tab) {
+    const int C = R / V;
+    const int64_t total = n * C;
+    const int ak = alpha_len == 1 ? 0 : k;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = t / C;
+        const int ch = static_cast<int>(t - i * C);
+        const int b = n_inst > 1 ? find_inst(inst_off, n_inst, i) : 0;
+        const XT a = alpha_tab[static_cast<int64_t>(b) * alpha_len + ak];
+        const XT bb = beta_tab[b];
+        XT acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = XT(0);
+        const int64_t e1 = __ldg(row_ptr + i + 1);
+        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
+            const int64_t j = __ldg(col + e);
+            const XT w = static_cast<XT>(__ldg(val + e));
+            XT xv[V];
+            ldv<XT, V>(xi + j * R + ch * V, xv);
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += w * xv[q];
+        }
+        XT xs[V], out[V];
+        ldv<XT, V>(xi + i * R + ch * V, xs);
+        const XT hi = h ? h[i] : XT(0);
+#pragma unroll
+        for (int q = 0; q < V; ++q) out[q] = dcbrt(scale_beta(acc[q] + a * xs[q] + hi, bb));
+        stv<XT, V>(xo + i * R + ch * V, out);
+    }
+}
+
+// One CTA per (instance b = blockIdx.y, replica r = blockIdx.x); shared
+// memory holds two copies of that instance's iterate for replica r.
+template <typename XT, typename VT>
+__global__ void __launch_bounds__(1024)
+csr_fused_kernel(XT *__restrict__ x, const int64_t *__restrict__ row_ptr,
+                 const int32_t *__restrict__ col, const VT *__restrict__ val,
+                 const XT *__restrict__ h, const int64_t *__restrict__ inst_off, int64_t n, int R,
+                 const double *__restrict__ alpha_tab, int alpha_len,
+                 const double *__restrict__ beta_tab, int iters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    XT *buf = reinterpret_cast<XT *>(smem_raw);
+    const int b = blockIdx.y, r = blockIdx.x;
+    const int64_t lo = inst_off ? inst_off[b] : 0;
+    const int64_t hi = inst_off ? inst_off[b + 1] : n;
+    const int nb = static_cast<int>(hi - lo);
+    XT *cur = buf, *nxt = buf + nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = x[(lo + i) * R + r];
+    const XT bb = static_cast<XT>(beta_tab[b]);
+    __syncthreads();
+    for (int k = 0; k < iters; ++k) {
+        const XT a = static_cast<XT>(alpha_tab[static_cast<int64_t>(b) * alpha_len +
+                                               (alpha_len == 1 ? 0 : k)]);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const int64_t row = lo + i;
+            XT acc = XT(0);
+            const int64_t e1 = __ldg(row_ptr + row + 1);
+            for (int64_t e = __ldg(row_ptr + row); e < e1; ++e)
+                acc += static_cast<XT>(__ldg(val + e)) * cur[__ldg(col + e) - lo];
+            const XT hv = h ? h[row] : XT(0);
+            nxt[i] = dcbrt((acc + a * cur[i] + hv) / bb);
+        }
+        __syncthreads();
+        XT *t = cur; cur = nxt; nxt = t;
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) x[(lo + i) * R + r] = cur[i];
+}
+
+template <typename XT, typename VT, int V>
+void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
+                 const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, cudaStream_t st) {
+    const int64_t total = c->n * (R / V);
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(c->num_sms) * 32;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    csr_step_kernel<XT, VT, V><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
+        c->n, R, alpha_tab, alpha_len, k, beta_tab);
+}
+
+template <typename XT, int V>
+ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
+                            const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab,
+                            cudaStream_t st) {
+    switch (c->jtype) {
+        case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
+        case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
+        case ISING_F32: launch_step<XT, float, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
+        case ISING_F64: launch_step<XT, double, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
+        default: return fail(ISING_ERR_UNSUPPORTED, "CSR value type not supported on the device");
+    }
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+template <typename XT, typename VT>
+ising_status_t launch_fused(const ising_context *c, XT *x, int R, const XT *h,
+                            const ParamTabs &p, int iters, cudaStream_t st) {
+    const size_t smem = 2 * static_cast<size_t>(c->max_inst_n) * sizeof(XT);
+    auto kern = csr_fused_kernel<XT, VT>;
+    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem)));
+    int threads = 1024;
+    if (c->max_inst_n < 1024) threads = static_cast<int>(((c->max_inst_n + 31) / 32) * 32);
+    if (threads < 32) threads = 32;
+    dim3 grid(static_cast<unsigned>(R), static_cast<unsigned>(c->n_inst));
+    kern<<<grid, threads, smem, st>>>(x, c->row_ptr, c->col, static_cast<const VT *>(c->val), h,
+                                      c->n_inst > 1 ? c->inst_off : nullptr, c->n, R, p.alpha_d,
+                                      p.alpha_len, p.beta_d, iters);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+template <typename XT>
+ising_status_t fused_dispatch(const ising_context *c, XT *x, int R, const XT *h,
+                              const ParamTabs &p, int iters, cudaStream_t st) {
+    switch (c->jtype) {
+        case ISING_I8: return launch_fused<XT, int8_t>(c, x, R, h, p, iters, st);
+        case ISING_I32: return launch_fused<XT, int32_t>(c, x, R, h, p, iters, st);
+        case ISING_F32: return launch_fused<XT, float>(c, x, R, h, p, iters, st);
+        case ISING_F64: return launch_fused<XT, double>(c, x, R, h, p, iters, st);
+        default: return fail(ISING_ERR_UNSUPPORTED, "CSR value type not supported on the device");
+    }
+}
+
+}  // namespace
+
+size_t csr_fused_max_spins(int xtype) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return static_cast<size_t>(optin) / (2 * (xtype == ISING_F64 ? 8 : 4));
+}
+
+ising_status_t csr_step(const ising_context *c, const void *xi, void *xo, int xtype, int R,
+                        const ParamTabs &p, int k, cudaStream_t st) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(xi) | reinterpret_cast<uintptr_t>(xo);
+    if (xtype == ISING_F32) {
+        const float *x_in = static_cast<const float *>(xi);
+        float *x_out = static_cast<float *>(xo);
+        if (R % 4 == 0 && a % 16 == 0)
+            return dispatch_val<float, 4>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
+        if (R % 2 == 0 && a % 8 == 0)
+            return dispatch_val<float, 2>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
+        return dispatch_val<float, 1>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
+    }
+    if (xtype == ISING_F64) {
+        const double *x_in = static_cast<const double *>(xi);
+        double *x_out = static_cast<double *>(xo);
+        if (R % 2 == 0 && a % 16 == 0)
+            return dispatch_val<double, 2>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, st);
+        return dispatch_val<double, 1>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, st);
+    }
+    return fail(ISING_ERR_UNSUPPORTED, "CSR iterate type must be F32 or F64");
+}
+
+ising_status_t csr_fused(const ising_context *c, void *x, int xtype, int R, const ParamTabs &p,
+                         int iters, cudaStream_t st) {
+    if (static_cast<size_t>(c->max_inst_n) > csr_fused_max_spins(xtype))
+        return ISING_ERR_UNSUPPORTED;
+    if (xtype == ISING_F64)
+        return fused_dispatch<double>(c, static_cast<double *>(x), R, c->h_f64, p, iters, st);
+    if (xtype == ISING_F32)
+        return fused_dispatch<float>(c, static_cast<float *>(x), R, c->h_f32, p, iters, st);
+    return ISING_ERR_UNSUPPORTED;
+}
+
+}  // namespace doch

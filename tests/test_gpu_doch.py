@@ -1,0 +1,303 @@
+"""GPU parity of the DOCH iteration and readout against the FP64 oracle.
+
+Every case feeds the same seeded inputs to the CUDA library (through the C
+ABI) and to the oracle, and compares element by element:
+  * FP32 iterates: max_r ||x_gpu - x_ref|| / ||x_ref|| <= 1e-5 (the FP32
+    tolerance of the accuracy bar, a vector criterion), and every element
+    within 10x that of max|x_ref|: a wrong neighbour or a missed tile seam
+    shows up as an O(1) error in one element. The element bound is looser
+    because a component whose sum u_i + alpha x_i nearly cancels is small,
+    and the cube root multiplies the FP32 rounding of that sum by
+    1 / (3 x_i^2);
+  * FP64 iterates: the same with 1e-10 (summation order only);
+  * integer energies and cuts of a given spin vector: bit-exact;
+  * FP64 energies: 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_01928_gb300 import _native as N
+from paper_2509_01928_gb300 import build as B
+from paper_2509_01928_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build_library()
+    return N.load()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _close(x_gpu, x_ref, tol):
+    x_gpu = np.asarray(x_gpu, dtype=np.float64).reshape(x_ref.shape)
+    if x_ref.ndim == 1:
+        x_ref = x_ref[:, None]
+        x_gpu = x_gpu[:, None]
+    rel = np.linalg.norm(x_gpu - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert rel.max() <= tol, f"relative L2 error {rel.max():.3e} > {tol}"
+    el = np.abs(x_gpu - x_ref).max() / np.abs(x_ref).max()
+    assert el <= 10 * tol, f"element error {el:.3e} > {10 * tol}"
+
+
+class Handle:
+    def __init__(self, J, h=None, instances=None, flags=0):
+        self.p = N.Problem(J, h, instances)
+        self.h = N.ising_create(self.p, flags)
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *a):
+        N.ising_destroy(self.h)
+
+
+# ---------------------------------------------------------------------------
+# 2-D torus (stencil) path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(37, 1028), (16, 2048), (5, 8), (2, 4), (9, 4)])
+@pytest.mark.parametrize("iters", [1, 7, 60])
+def test_torus_fp32_r1(shape, iters):
+    t = I.torus_pm1(*shape, seed=101)
+    x0 = I.x0_uniform(t.n, 1, seed=102)
+    alpha, beta = O.alpha_beta(t, eta=1.0, method="wigner")
+    ref = O.doch(O.Problem(t), x0, alpha, beta, iters)
+    with Handle(t) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], iters)
+        _close(x.cpu().numpy(), ref, TOL32)
+
+
+@pytest.mark.parametrize("shape, R, dtype", [((13, 11), 3, np.float32), ((6, 10), 4, np.float64),
+                                             ((7, 9), 1, np.float64), ((3, 6), 1, np.float32)])
+def test_torus_generic(shape, R, dtype):
+    t = I.torus_pm1(*shape, seed=103)
+    x0 = I.x0_uniform(t.n, R, seed=104, dtype=dtype)
+    alpha, beta = O.alpha_beta(t, eta=1.0, method="eig")
+    ref = O.doch(O.Problem(t), x0, alpha, beta, 25)
+    with Handle(t) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], 25)
+        _close(x.cpu().numpy(), ref, TOL32 if dtype == np.float32 else TOL64)
+
+
+def test_torus_host_buffers_match_device():
+    t = I.torus_pm1(20, 64, seed=105)
+    x0 = I.x0_uniform(t.n, 1, seed=106)
+    alpha, beta = O.alpha_beta(t, method="wigner")
+    with Handle(t) as h:
+        xd = _dev(x0)
+        N.ising_iterate(h, xd, [alpha], [beta], 9)
+        xh = x0.copy()
+        N.ising_iterate(h, xh, [alpha], [beta], 9)
+        assert np.array_equal(xh, xd.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# CSR path
+# ---------------------------------------------------------------------------
+
+def test_csr_fp64_er800_plain_method():
+    """Erdos-Renyi n = 800, p = 0.06, +-1, FP64, R = 8, 1000 iterations."""
+    g = I.erdos_renyi_pm1(800, 0.06, seed=1)
+    x0 = I.x0_uniform(g.n, 8, seed=2, dtype=np.float64)
+    alpha, beta = O.alpha_beta(g, eta=1.0, method="eig")
+    ref = O.doch(O.Problem(g), x0, alpha, beta, 1000)
+    with Handle(g) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], 1000)
+        _close(x.cpu().numpy(), ref, TOL64)
+        E = torch.zeros(8, dtype=torch.int64, device="cuda")
+        cut = torch.zeros(8, dtype=torch.int64, device="cuda")
+        best = torch.zeros(1, dtype=torch.int32, device="cuda")
+        N.ising_energy(h, x, E_int=E, cut_int=cut, best=best)
+        s_ref = O.sign(ref)
+        s_gpu = O.sign(x.cpu().numpy())
+        if np.array_equal(s_ref, s_gpu):   # energies are unique only for equal spins
+            Er, cr = O.energy_int(O.Problem(g), s_ref)
+            assert np.array_equal(E.cpu().numpy(), Er)
+            assert np.array_equal(cut.cpu().numpy(), cr)
+            assert best.item() == int(np.argmin(Er))
+
+
+@pytest.mark.parametrize("R", [64, 6, 1])
+def test_csr_fp32_regular(R):
+    g = I.regular_pm1(3000, 3, seed=3)
+    x0 = I.x0_uniform(g.n, R, seed=4)
+    alpha, beta = O.alpha_beta(g, eta=1.0, method="eig")
+    ref = O.doch(O.Problem(g), x0, alpha, beta, 30)
+    with Handle(g) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], 30)
+        _close(x.cpu().numpy(), ref, TOL32)
+
+
+def test_csr_fp32_large_uses_step_kernel():
+    """An instance too large for shared memory runs one launch per step."""
+    g = I.regular_pm1(70000, 3, seed=5)
+    x0 = I.x0_uniform(g.n, 4, seed=6)
+    alpha, beta = O.alpha_beta(g, eta=1.0, method="wigner")
+    ref = O.doch(O.Problem(g), x0, alpha, beta, 12)
+    with Handle(g) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], 12)
+        _close(x.cpu().numpy(), ref, TOL32)
+
+
+def test_csr_alpha_schedule():
+    g = I.regular_pm1(500, 4, seed=7)
+    x0 = I.x0_uniform(g.n, 8, seed=8)
+    a0, beta = O.alpha_beta(g, eta=1.0, method="eig")
+    sched = a0 * (1.0 + 0.3 * np.sin(np.arange(40) / 5.0))
+    ref = O.doch(O.Problem(g), x0, sched, beta, 40)
+    with Handle(g) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, sched, [beta], 40)
+        _close(x.cpu().numpy(), ref, TOL32)
+
+
+def _batch(sizes, degrees, seed, with_h=True):
+    gs = [I.regular_gauss(int(n), int(d), seed=seed + b) for b, (n, d) in enumerate(zip(sizes, degrees))]
+    hs = [I.field_gauss(g.n, 0.1, seed=seed + 1000 + b) for b, g in enumerate(gs)]
+    off = np.cumsum([0] + [g.n for g in gs]).astype(np.int64)
+    nz = np.cumsum([0] + [g.nnz for g in gs])
+    rp = np.concatenate([[0]] + [g.row_ptr[1:] + z for g, z in zip(gs, nz[:-1])])
+    col = np.concatenate([g.col + o for g, o in zip(gs, off[:-1])]).astype(np.int32)
+    val = np.concatenate([g.val for g in gs])
+    h = np.concatenate(hs) if with_h else None
+    return gs, hs, I.CSR(off[-1], rp, col, val), h, off
+
+
+@pytest.mark.parametrize("xdtype, jdtype", [(np.float32, np.float32), (np.float64, np.float64)])
+def test_csr_batched_uneven_with_field(xdtype, jdtype):
+    sizes, degrees = [500, 1733, 64, 900], [3, 10, 5, 8]
+    gs, hs, J, h, off = _batch(sizes, degrees, seed=20)
+    J.val = J.val.astype(jdtype)
+    h = h.astype(jdtype)
+    R = 16
+    x0 = I.x0_uniform(int(off[-1]), R, seed=21, dtype=xdtype)
+    alphas, betas = zip(*[O.alpha_beta(g, eta=1.0, method="eig") for g in gs])
+    iters = 40
+    with Handle(J, h, off) as hd:
+        x = _dev(x0)
+        N.ising_iterate(hd, x, list(alphas), list(betas), iters, n_instances=len(gs))
+        xg = x.cpu().numpy()
+    for b, g in enumerate(gs):
+        ref = O.doch(O.Problem(g, hs[b].astype(jdtype)), x0[off[b]:off[b + 1]], alphas[b], betas[b], iters)
+        _close(xg[off[b]:off[b + 1]], ref, TOL32 if xdtype == np.float32 else TOL64)
+
+
+# ---------------------------------------------------------------------------
+# energies and cuts of given (seeded) spin vectors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["torus", "torus_vec", "er"])
+def test_energy_integer_exact(kind):
+    if kind == "torus":
+        J = I.torus_pm1(33, 17, seed=30)
+    elif kind == "torus_vec":
+        J = I.torus_pm1(64, 1024, seed=31)
+    else:
+        J = I.erdos_renyi_pm1(800, 0.06, seed=32)
+    n = J.n
+    R = 5
+    x = I.x0_uniform(n, R, seed=33)      # seeded reals: the sign is taken on both sides
+    x[::97] = 0.0                        # exact zeros: sign(0) = +1
+    s = O.sign(x.astype(np.float64))
+    Er, cr = O.energy_int(O.Problem(J), s)
+    with Handle(J) as h:
+        for xin in (_dev(x), _dev(s), x):  # F32 device, I8 spins, F32 host
+            E = np.zeros(R, np.int64)
+            cut = np.zeros(R, np.int64)
+            best = np.zeros(1, np.int32)
+            sp = np.zeros((n, R), np.int8)
+            N.ising_energy(h, xin, E_int=E, cut_int=cut, best=best, spins=sp)
+            assert np.array_equal(E, Er)
+            assert np.array_equal(cut, cr)
+            assert best[0] == int(np.argmin(Er))
+            assert np.array_equal(sp, s)
+
+
+def test_energy_f64_batched_gaussian():
+    sizes, degrees = [700, 1200, 300], [3, 9, 6]
+    gs, hs, J, h, off = _batch(sizes, degrees, seed=40)
+    R = 16
+    x = I.x0_uniform(int(off[-1]), R, seed=41)
+    with Handle(J, h, off) as hd:
+        E1 = np.zeros((3, R))
+        c1 = np.zeros((3, R))
+        best = np.zeros(3, np.int32)
+        N.ising_energy(hd, _dev(x), E_f64=E1, cut_f64=c1, best=best)
+        E2 = np.zeros((3, R))
+        N.ising_energy(hd, _dev(x), E_f64=E2)
+        assert np.array_equal(E1, E2)     # fixed reduction order: identical run to run
+        with pytest.raises(N.IsingError):  # no exact energy for real couplings
+            N.ising_energy(hd, _dev(x), E_int=np.zeros((3, R), np.int64))
+    for b, g in enumerate(gs):
+        s = O.sign(x[off[b]:off[b + 1]].astype(np.float64))
+        Er, cr = O.energy(O.Problem(g, hs[b]), s)
+        np.testing.assert_allclose(E1[b], Er, rtol=1e-12)
+        np.testing.assert_allclose(c1[b], cr, rtol=1e-12, atol=1e-9)
+        assert best[b] == int(np.argmin(Er))
+
+
+# ---------------------------------------------------------------------------
+# FP64 Hamiltonian monitor
+# ---------------------------------------------------------------------------
+
+def test_hamiltonian_trace_fp64():
+    g = I.erdos_renyi_pm1(200, 0.1, seed=50)
+    h = np.round(2 * I.field_gauss(200, 0.1, seed=51)).astype(np.int8)
+    alpha, beta = O.alpha_beta(g, eta=1.1, method="eig")
+    beta /= 200 ** 1.5
+    x0 = I.x0_uniform(g.n, 4, seed=52, dtype=np.float64)
+    ref, Href = O.doch(O.Problem(g, h), x0, alpha, beta, 15, trace=True)
+    with Handle(g, h, flags=N.FLAG_STRICT_MONOTONE) as hd:
+        x = _dev(x0)
+        H = np.zeros((16, 1, 4))
+        N.ising_iterate(hd, x, [alpha], [beta], 15, H_trace=H)
+        _close(x.cpu().numpy(), ref, TOL64)
+        np.testing.assert_allclose(H[:, 0, :], Href, rtol=1e-10, atol=1e-12 * np.abs(Href).max())
+
+
+def test_hamiltonian_trace_torus_fp32_monotone():
+    t = I.torus_pm1(32, 64, seed=53)
+    alpha, beta = O.alpha_beta(t, eta=1.05, method="eig")
+    x0 = I.x0_uniform(t.n, 1, seed=54)
+    with Handle(t) as hd:
+        x = _dev(x0)
+        H = torch.zeros((21, 1, 1), dtype=torch.float64, device="cuda")
+        N.ising_iterate(hd, x, [alpha], [beta], 20, H_trace=H)
+        Hh = H.cpu().numpy().ravel()
+    _, Href = O.doch(O.Problem(t), x0, alpha, beta, 20, trace=True)
+    np.testing.assert_allclose(Hh, Href.ravel(), rtol=1e-4)
+    assert np.all(np.diff(Hh) <= 1e-6 * np.abs(Hh).max())
+
+
+# ---------------------------------------------------------------------------
+# argument errors reach the caller as statuses
+# ---------------------------------------------------------------------------
+
+def test_iterate_argument_errors():
+    t = I.torus_pm1(8, 8, seed=60)
+    with Handle(t) as h:
+        x = _dev(I.x0_uniform(t.n, 1, seed=61))
+        with pytest.raises(N.IsingError) as e:
+            N.ising_iterate(h, x, [1.0], [0.0], 3)
+        assert e.value.name == "ISING_ERR_INVALID_ARG"
+        with pytest.raises(N.IsingError) as e:
+            N.ising_iterate(h, x, [np.inf], [1.0], 3)
+        assert e.value.name == "ISING_ERR_NONFINITE"
+        with pytest.raises(N.IsingError):
+            N.ising_iterate(h, x, [1.0, 2.0], [1.0], 3)   # alpha_len neither 1 nor iters
