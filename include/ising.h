@@ -219,6 +219,15 @@ ISING_API ising_status_t ising_synchronize(ising_handle_t h, void *stream);
 /* Problem size of a handle: total spins and instance count. */
 ISING_API ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances);
 
+/*
+ * Diagnostic: the FP32 cube root of the stencil kernel, sign(z) 2^(log2|z|/3)
+ * evaluated on z 2^(-3k) and rescaled by 2^k, written to ours[i], next to
+ * CUDA's cbrtf(z[i]) in ref[i]. z, ours, ref are device arrays of n floats;
+ * -40 <= k <= 40. Synchronises the stream.
+ */
+ISING_API ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
+                                             int32_t k, void *stream);
+
 /* Static description of a status code. */
 ISING_API const char *ising_status_string(ising_status_t s);
 

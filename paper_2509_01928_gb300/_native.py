@@ -74,6 +74,8 @@ def load():
                                    ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
     lib.ising_synchronize.argtypes = [_vp, _vp]
     lib.ising_get_size.argtypes = [_vp, _vp, _vp]
+    lib.ising_selftest_cbrt.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]
+    lib.ising_selftest_cbrt.restype = ctypes.c_int
     lib.ising_status_string.argtypes = [ctypes.c_int]
     lib.ising_status_string.restype = ctypes.c_char_p
     lib.ising_last_error.argtypes = []

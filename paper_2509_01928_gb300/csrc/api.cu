@@ -495,7 +495,7 @@ ising_status_t step(ising_context *c, const void *xi, void *xo, int xtype, int R
         const double a = alpha_h[p.alpha_len == 1 ? 0 : k];
         if (xtype == ISING_F32)
             return torus_step_f32(c, static_cast<const float *>(xi), static_cast<float *>(xo), R,
-                                  static_cast<float>(a), static_cast<float>(1.0 / beta_h[0]), st);
+                                  static_cast<float>(a), 1.0 / beta_h[0], st);
         return torus_step_f64(c, static_cast<const double *>(xi), static_cast<double *>(xo), R, a,
                               beta_h[0], st);
     }

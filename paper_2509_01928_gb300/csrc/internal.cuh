@@ -103,7 +103,7 @@ namespace doch {
 
 // TORUS2D, one DOCH step, x_out = T(x_in) (Eq. FPE). XT = float or double.
 ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *x_out, int R,
-                              float alpha, float inv_beta, cudaStream_t st);
+                              float alpha, double inv_beta, cudaStream_t st);
 ising_status_t torus_step_f64(const ising_context *c, const double *x_in, double *x_out, int R,
                               double alpha, double beta, cudaStream_t st);
 

@@ -1,0 +1,37 @@
+// Diagnostic entry point: the device cube root of the stencil kernel next to
+// CUDA's cbrtf on the same inputs (see ising_selftest_cbrt in ising.h).
+#include "cbrt.cuh"
+#include "internal.cuh"
+
+namespace doch {
+namespace {
+
+__global__ void cbrt_pair(const float *__restrict__ z, float *__restrict__ ours,
+                          float *__restrict__ ref, int64_t n, float zscale, float xscale) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        ours[i] = cbrt_pow2(z[i] * zscale) * xscale;
+        ref[i] = cbrtf(z[i]);
+    }
+}
+
+}  // namespace
+}  // namespace doch
+
+extern "C" ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
+                                              int32_t k, void *stream) {
+    using namespace doch;
+    if (!z || !ours || !ref || n < 0 || k < -40 || k > 40)
+        return fail(ISING_ERR_INVALID_ARG, "selftest_cbrt: bad argument");
+    if (n == 0) return ISING_OK;
+    int dev = 0, sms = 1;
+    DOCH_CUDA(cudaGetDevice(&dev));
+    DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
+    cbrt_pair<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        z, ours, ref, n, std::ldexp(1.0f, -3 * k), std::ldexp(1.0f, k));
+    DOCH_CUDA(cudaGetLastError());
+    DOCH_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return ISING_OK;
+}

@@ -7,13 +7,23 @@
 // Fast path (R = 1, FP32, l_cols % 4 == 0, 16-byte aligned rows): a CTA of
 // 256 threads owns a tile of 1024 columns and a contiguous strip of rows.
 // Each thread owns 4 columns (one float4 of x, one packed word of four int8
-// couplings per row), walks down its strip keeping x rows r-1, r, r+1 and
-// down rows r-1, r in registers, and prefetches the next row one step ahead.
-// Horizontal neighbours come from the adjacent lanes by warp shuffles; the
-// two edge lanes of a warp (and the lanes at the periodic seam) load their
-// halo value from global memory. Per site and step the kernel reads x once
-// (4 B), both couplings once (2 B) and writes x once (4 B), plus 2 extra x
-// rows per strip.
+// couplings per row), walks down its strip keeping x rows r-1, r, r+1 and the
+// down couplings of row r-1 (already converted) in registers, and prefetches
+// the loads of the next row one step ahead. Horizontal neighbours come from
+// the adjacent lanes by warp shuffles; lane 0 loads the left halo (and the
+// coupling to it), lane 31 the right halo. Lanes past the last column of the
+// lattice read wrapped columns, so the shuffles at the periodic seam deliver
+// column 0. Per site and step the kernel reads x once (4 B), both couplings
+// once (2 B) and writes x once (4 B), plus 2 extra x rows per strip.
+//
+// Cube root: cbrt(z) = 2^(k) * exp2( log2(|z| 2^(-3k)) / 3 ) with sign, using
+// the hardware base-2 logarithm/exponential approximations (PTX lg2.approx,
+// ex2.approx). The exact power-of-two prescale 2^(-3k) is folded into 1/beta
+// (k chosen on the host from beta) so |log2| stays small and the FP32 log
+// keeps its precision; relative error ~2^-22.
+#include <cmath>
+
+#include "cbrt.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -22,93 +32,89 @@ namespace {
 constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int64_t wrap(int64_t i, int64_t L) {
-    return i < 0 ? i + L : (i >= L ? i - L : i);
-}
-
 // sign-extended byte k (0..3) of a packed word of four int8
 __device__ __forceinline__ float sbyte(int v, int k) {
     return static_cast<float>((v << (24 - 8 * k)) >> 24);
 }
 
-__global__ void __launch_bounds__(kThreads)
+// 40 registers: 6 CTAs (1536 threads) per SM keep enough loads in flight
+__global__ void __launch_bounds__(kThreads, 6)
 torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
-                  const int8_t *__restrict__ right, const int8_t *__restrict__ down,
-                  int64_t Lr, int64_t Lc, int tiles, int bpt, float alpha, float inv_beta) {
+                  const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
+                  int tiles, int bpt, float alpha, float zscale, float xscale) {
     const int tile = blockIdx.x % tiles;
     const int part = blockIdx.x / tiles;
-    const int64_t r0 = Lr * part / bpt, r1 = Lr * (part + 1) / bpt;
+    const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
+    const int r1 = static_cast<int>(static_cast<int64_t>(Lr) * (part + 1) / bpt);
     if (r0 >= r1) return;  // uniform over the block
 
-    const int64_t ncol4 = Lc >> 2;
-    const int64_t c4 = static_cast<int64_t>(tile) * kThreads + threadIdx.x;
-    const bool active = c4 < ncol4;
-    const int64_t c = c4 * 4;
+    const int ncol4 = Lc >> 2;
+    const int c4raw = tile * kThreads + threadIdx.x;
+    const bool active = c4raw < ncol4;
+    const int c4 = c4raw % ncol4;
+    const int c = c4 * 4;
     const int lane = threadIdx.x & 31;
-    // halo columns: a lane whose neighbour lane does not hold them loads them
-    const bool need_l = active && (lane == 0 || c == 0);
-    const bool need_r = active && (lane == 31 || c + 4 >= Lc);
-    const int64_t cl = (c == 0) ? Lc - 1 : c - 1;
-    const int64_t cr = (c + 4 >= Lc) ? 0 : c + 4;
+    const bool is_l = lane == 0, is_r = lane == 31;
+    const int hcol = is_l ? (c == 0 ? Lc - 1 : c - 1) : (c + 4 >= Lc ? 0 : c + 4);
+    const int64_t n = static_cast<int64_t>(Lr) * Lc;
+    const float *xc = xi + c;
+    const int8_t *rc = right + c, *dc = down + c;
+    const float *hx = xi + hcol;
+    const int8_t *hw = right + hcol;
+    float *oc = xo + c;
+    auto ldx = [&](int64_t o) -> float4 { return __ldg(reinterpret_cast<const float4 *>(xc + o)); };
+    auto ldw = [&](const int8_t *p, int64_t o) -> int { return __ldg(reinterpret_cast<const int *>(p + o)); };
+    auto ldh = [&](int64_t o) -> float { return (is_l || is_r) ? __ldg(hx + o) : 0.f; };
 
-    auto ldx = [&](int64_t r) -> float4 {
-        return active ? __ldg(reinterpret_cast<const float4 *>(xi + r * Lc) + c4)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    };
-    auto ldw = [&](const int8_t *p, int64_t r) -> int {
-        return active ? __ldg(reinterpret_cast<const int *>(p + r * Lc) + c4) : 0;
-    };
-    auto ldhx = [&](bool need, int64_t r, int64_t cc) -> float {
-        return need ? __ldg(xi + r * Lc + cc) : 0.f;
-    };
-
-    int64_t r = r0;
-    float4 xu = ldx(wrap(r - 1, Lr));
-    float4 xm = ldx(r);
-    float hlm = ldhx(need_l, r, cl), hrm = ldhx(need_r, r, cr);
-    int du = ldw(down, wrap(r - 1, Lr));
-    // pending loads for row r: x row r+1 (+ halos), down row r, right row r (+ left halo)
-    int64_t rp = wrap(r + 1, Lr);
-    float4 xd_n = ldx(rp);
-    float hld_n = ldhx(need_l, rp, cl), hrd_n = ldhx(need_r, rp, cr);
-    int dm_n = ldw(down, r), rt_n = ldw(right, r);
-    float wl_n = need_l ? static_cast<float>(__ldg(right + r * Lc + cl)) : 0.f;
-
-    for (; r < r1; ++r) {
-        const float4 xd = xd_n;
-        const float hld = hld_n, hrd = hrd_n;
-        const int dm = dm_n, rt = rt_n;
-        const float wl = wl_n;
+    int64_t o = static_cast<int64_t>(r0) * Lc;        // row r
+    const int64_t ou = o == 0 ? n - Lc : o - Lc;       // row r-1
+    int64_t od = o + Lc == n ? 0 : o + Lc;             // row r+1
+    float4 xu = ldx(ou), xm = ldx(o);
+    float hm = ldh(o);
+    const int dup = ldw(dc, ou);
+    float du0 = sbyte(dup, 0), du1 = sbyte(dup, 1), du2 = sbyte(dup, 2), du3 = sbyte(dup, 3);
+    float4 xd = ldx(od);
+    float hd = ldh(od);
+    int dm = ldw(dc, o), rt = ldw(rc, o);
+    float wl = is_l ? static_cast<float>(__ldg(hw + o)) : 0.f;
+    for (int r = r0; r < r1; ++r) {
+        const int64_t on = od;                            // row r+1
+        const int64_t onn = on + Lc == n ? 0 : on + Lc;   // row r+2
+        float4 xn = xd;
+        float hn = hd, wn = wl;
+        int dn = dm, rn = rt;
         if (r + 1 < r1) {  // prefetch the loads of row r+1
-            const int64_t rn = r + 1, rnn = wrap(r + 2, Lr);
-            xd_n = ldx(rnn);
-            hld_n = ldhx(need_l, rnn, cl);
-            hrd_n = ldhx(need_r, rnn, cr);
-            dm_n = ldw(down, rn);
-            rt_n = ldw(right, rn);
-            wl_n = need_l ? static_cast<float>(__ldg(right + rn * Lc + cl)) : 0.f;
+            xn = ldx(onn);
+            hn = ldh(onn);
+            dn = ldw(dc, on);
+            rn = ldw(rc, on);
+            wn = is_l ? static_cast<float>(__ldg(hw + on)) : 0.f;
         }
         // horizontal neighbours of row r and the coupling to the left neighbour
         float xl = __shfl_up_sync(kFull, xm.w, 1);
         float xr = __shfl_down_sync(kFull, xm.x, 1);
-        const int rt_left = __shfl_up_sync(kFull, rt, 1);
-        float wleft = sbyte(rt_left, 3);
-        if (need_l) { xl = hlm; wleft = wl; }
-        if (need_r) xr = hrm;
+        const int rtl = __shfl_up_sync(kFull, rt, 1);
+        float wleft = sbyte(rtl, 3);
+        if (is_l) { xl = hm; wleft = wl; }
+        if (is_r) xr = hm;
 
         const float w0 = sbyte(rt, 0), w1 = sbyte(rt, 1), w2 = sbyte(rt, 2), w3 = sbyte(rt, 3);
-        float u0 = w0 * xm.y + wleft * xl + sbyte(dm, 0) * xd.x + sbyte(du, 0) * xu.x;
-        float u1 = w1 * xm.z + w0 * xm.x + sbyte(dm, 1) * xd.y + sbyte(du, 1) * xu.y;
-        float u2 = w2 * xm.w + w1 * xm.y + sbyte(dm, 2) * xd.z + sbyte(du, 2) * xu.z;
-        float u3 = w3 * xr + w2 * xm.z + sbyte(dm, 3) * xd.w + sbyte(du, 3) * xu.w;
+        const float d0 = sbyte(dm, 0), d1 = sbyte(dm, 1), d2 = sbyte(dm, 2), d3 = sbyte(dm, 3);
+        const float u0 = w0 * xm.y + wleft * xl + d0 * xd.x + du0 * xu.x;
+        const float u1 = w1 * xm.z + w0 * xm.x + d1 * xd.y + du1 * xu.y;
+        const float u2 = w2 * xm.w + w1 * xm.y + d2 * xd.z + du2 * xu.z;
+        const float u3 = w3 * xr + w2 * xm.z + d3 * xd.w + du3 * xu.w;
         float4 out;
-        out.x = cbrtf((u0 + alpha * xm.x) * inv_beta);
-        out.y = cbrtf((u1 + alpha * xm.y) * inv_beta);
-        out.z = cbrtf((u2 + alpha * xm.z) * inv_beta);
-        out.w = cbrtf((u3 + alpha * xm.w) * inv_beta);
-        if (active) __stcs(reinterpret_cast<float4 *>(xo + r * Lc) + c4, out);
+        out.x = cbrt_pow2((u0 + alpha * xm.x) * zscale) * xscale;
+        out.y = cbrt_pow2((u1 + alpha * xm.y) * zscale) * xscale;
+        out.z = cbrt_pow2((u2 + alpha * xm.z) * zscale) * xscale;
+        out.w = cbrt_pow2((u3 + alpha * xm.w) * zscale) * xscale;
+        if (active) __stcs(reinterpret_cast<float4 *>(oc + o), out);
 
-        xu = xm; xm = xd; hlm = hld; hrm = hrd; du = dm;
+        xu = xm; xm = xd; hm = hd;
+        du0 = d0; du1 = d1; du2 = d2; du3 = d3;
+        xd = xn; hd = hn; dm = dn; rt = rn; wl = wn;
+        o = on; od = onn;
     }
 }
 
@@ -152,11 +158,11 @@ int vec4_blocks_per_sm() {
 }  // namespace
 
 ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *x_out, int R,
-                              float alpha, float inv_beta, cudaStream_t st) {
+                              float alpha, double inv_beta, cudaStream_t st) {
     const int64_t Lr = c->l_rows, Lc = c->l_cols;
     const bool aligned = (reinterpret_cast<uintptr_t>(x_in) % 16 == 0) &&
                          (reinterpret_cast<uintptr_t>(x_out) % 16 == 0);
-    if (R == 1 && Lc % 4 == 0 && aligned) {
+    if (R == 1 && Lc % 4 == 0 && aligned && Lr < (1LL << 31) && Lc < (1LL << 31)) {
         const int64_t ncol4 = Lc / 4;
         const int tiles = static_cast<int>((ncol4 + kThreads - 1) / kThreads);
         const int64_t slots = static_cast<int64_t>(c->num_sms) * vec4_blocks_per_sm();
@@ -164,15 +170,19 @@ ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *
         if (bpt < 1) bpt = 1;
         if (bpt > Lr / 4) bpt = Lr / 4 > 0 ? Lr / 4 : 1;
         const int64_t blocks = bpt * tiles;
+        const int k = cbrt_prescale_exp(inv_beta);
+        const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+        const float xscale = std::ldexp(1.0f, -k);
         torus_f32_r1_vec4<<<static_cast<unsigned>(blocks), kThreads, 0, st>>>(
-            x_in, x_out, c->right, c->down, Lr, Lc, tiles, static_cast<int>(bpt), alpha, inv_beta);
+            x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), tiles,
+            static_cast<int>(bpt), alpha, zscale, xscale);
     } else {
         const int64_t total = Lr * Lc * R;
         int64_t blocks = (total + 255) / 256;
         const int64_t cap = static_cast<int64_t>(c->num_sms) * 16;
         if (blocks > cap) blocks = cap;
         torus_generic<float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-            x_in, x_out, c->right, c->down, Lr, Lc, R, alpha, inv_beta);
+            x_in, x_out, c->right, c->down, Lr, Lc, R, alpha, static_cast<float>(inv_beta));
     }
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;

@@ -10,6 +10,14 @@ ABI) and to the oracle, and compares element by element:
     and the cube root multiplies the FP32 rounding of that sum by
     1 / (3 x_i^2);
   * FP64 iterates: the same with 1e-10 (summation order only);
+  * FP32 iterates on graphs with weakly stable fixed points (random
+    regular graphs): some replicas drift from the FP64 trajectory by more
+    than 1e-5 under FP32 rounding alone, because the iteration contracts
+    slowly there. For those tests each replica r must satisfy
+    rel_r <= max(1e-5, 16 delta_r), where delta_r is the drift of the oracle
+    trajectory when every step's output is perturbed by one FP32 rounding
+    (relative 2^-24, seeded signs), and the median replica must be within
+    1e-5;
   * integer energies and cuts of a given spin vector: bit-exact;
   * FP64 energies: 1e-12 relative.
 """
@@ -48,6 +56,30 @@ def _close(x_gpu, x_ref, tol):
     assert rel.max() <= tol, f"relative L2 error {rel.max():.3e} > {tol}"
     el = np.abs(x_gpu - x_ref).max() / np.abs(x_ref).max()
     assert el <= 10 * tol, f"element error {el:.3e} > {10 * tol}"
+
+
+def _fp32_drift(P, x0, alpha, beta, iters):
+    """Relative drift per replica of the oracle trajectory under one FP32
+    rounding per component and step (max over two seeded sign patterns)."""
+    ref = O.doch(P, x0, alpha, beta, iters)
+    a = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (iters,))
+    out = np.zeros(ref.shape[1])
+    for seed in (1, 2):
+        x = np.asarray(x0, dtype=np.float64)
+        for j in range(iters):
+            x = O.doch(P, x, a[j], beta, 1)
+            sg = I.signs(I.stream_seed(seed, 200 + j), 0, x.size).reshape(x.shape)
+            x = x * (1.0 + sg * 2.0 ** -24)
+        out = np.maximum(out, np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0))
+    return ref, out
+
+
+def _close32_conditioned(x_gpu, ref, drift):
+    x_gpu = np.asarray(x_gpu, dtype=np.float64).reshape(ref.shape)
+    rel = np.linalg.norm(x_gpu - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    bound = np.maximum(TOL32, 16.0 * drift)
+    assert np.all(rel <= bound), f"replica error {rel.max():.3e} above its bound {bound[np.argmax(rel)]:.3e}"
+    assert np.median(rel) <= TOL32, f"median replica error {np.median(rel):.3e} > {TOL32}"
 
 
 class Handle:
@@ -136,11 +168,11 @@ def test_csr_fp32_regular(R):
     g = I.regular_pm1(3000, 3, seed=3)
     x0 = I.x0_uniform(g.n, R, seed=4)
     alpha, beta = O.alpha_beta(g, eta=1.0, method="eig")
-    ref = O.doch(O.Problem(g), x0, alpha, beta, 30)
+    ref, drift = _fp32_drift(O.Problem(g), x0, alpha, beta, 30)
     with Handle(g) as h:
         x = _dev(x0)
         N.ising_iterate(h, x, [alpha], [beta], 30)
-        _close(x.cpu().numpy(), ref, TOL32)
+        _close32_conditioned(x.cpu().numpy(), ref, drift)
 
 
 def test_csr_fp32_large_uses_step_kernel():
@@ -148,11 +180,11 @@ def test_csr_fp32_large_uses_step_kernel():
     g = I.regular_pm1(70000, 3, seed=5)
     x0 = I.x0_uniform(g.n, 4, seed=6)
     alpha, beta = O.alpha_beta(g, eta=1.0, method="wigner")
-    ref = O.doch(O.Problem(g), x0, alpha, beta, 12)
+    ref, drift = _fp32_drift(O.Problem(g), x0, alpha, beta, 12)
     with Handle(g) as h:
         x = _dev(x0)
         N.ising_iterate(h, x, [alpha], [beta], 12)
-        _close(x.cpu().numpy(), ref, TOL32)
+        _close32_conditioned(x.cpu().numpy(), ref, drift)
 
 
 def test_csr_alpha_schedule():
@@ -160,11 +192,11 @@ def test_csr_alpha_schedule():
     x0 = I.x0_uniform(g.n, 8, seed=8)
     a0, beta = O.alpha_beta(g, eta=1.0, method="eig")
     sched = a0 * (1.0 + 0.3 * np.sin(np.arange(40) / 5.0))
-    ref = O.doch(O.Problem(g), x0, sched, beta, 40)
+    ref, drift = _fp32_drift(O.Problem(g), x0, sched, beta, 40)
     with Handle(g) as h:
         x = _dev(x0)
         N.ising_iterate(h, x, sched, [beta], 40)
-        _close(x.cpu().numpy(), ref, TOL32)
+        _close32_conditioned(x.cpu().numpy(), ref, drift)
 
 
 def _batch(sizes, degrees, seed, with_h=True):
@@ -301,3 +333,37 @@ def test_iterate_argument_errors():
         assert e.value.name == "ISING_ERR_NONFINITE"
         with pytest.raises(N.IsingError):
             N.ising_iterate(h, x, [1.0, 2.0], [1.0], 3)   # alpha_len neither 1 nor iters
+
+
+# ---------------------------------------------------------------------------
+# device cube root of the stencil kernel against CUDA's cbrtf
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [0, 21, -7])
+def test_stencil_cube_root_accuracy(k):
+    """Relative error of the stencil's cube root against cbrtf over prescaled
+    arguments z' = z 2^(-3k) in [2^-60, 2^60]; odd; cbrt(0) = 0.
+
+    Bound derived from the arithmetic: the FP32 value l = log2|z'| carries an
+    absolute rounding of |l| 2^-24, which exp2(l / 3) turns into a relative
+    error of (ln 2 / 3) |l| 2^-24 < 0.25 |l| 2^-24; the hardware log2/exp2
+    approximations and the final products add about 2^-21. In the iteration
+    |l| stays small (z' ~ 1 at the attractor scale)."""
+    u = I.uniform01(I.stream_seed(9, k + 50), 0, 1 << 20)
+    e = -60.0 + 120.0 * u                              # log2 of the prescaled magnitude
+    sg = I.signs(I.stream_seed(9, k + 51), 0, 1 << 20)
+    z = (sg * np.exp2(e + 3 * k)).astype(np.float32)
+    z = np.concatenate([z, -z[:1000], np.zeros(4, np.float32)])
+    zd = _dev(z)
+    ours = torch.empty_like(zd)
+    ref = torch.empty_like(zd)
+    st = N.load().ising_selftest_cbrt(N._ptr(zd), N._ptr(ours), N._ptr(ref), z.size, k, None)
+    assert st == 0
+    o, r = ours.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+    nz = r != 0
+    rel = np.abs(o[nz] - r[nz]) / np.abs(r[nz])
+    lz = np.abs(np.log2(np.abs(z[nz].astype(np.float64))) - 3 * k)
+    bound = 2.0 ** -21 + 0.25 * lz * 2.0 ** -24
+    assert np.all(rel <= bound), (rel / bound).max()
+    assert np.array_equal(np.sign(o), np.sign(r))
+    assert np.all(o[-4:] == 0.0)
