@@ -220,6 +220,36 @@ ISING_API ising_status_t ising_synchronize(ising_handle_t h, void *stream);
 ISING_API ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances);
 
 /*
+ * Energy and cut of a TORUS2D lattice that allocates no device memory.
+ * (The paper has no counterpart: this is a deployment variant of the
+ * readout of ising_energy.)
+ *
+ * For callers that cannot call cudaMalloc -- code whose device memory is
+ * owned by another allocator that has reserved the device, or loops in which
+ * an allocation (which may synchronise the device) is not acceptable. It
+ * needs no handle: the caller passes the lattice couplings right/down
+ * ([l_rows][l_cols] int8, as in ising_problem_t), the FP32 iterates x
+ * ([n][R], n = l_rows * l_cols) and the outputs E_out / cut_out ([R] int64,
+ * either may be NULL), all as DEVICE arrays; host arrays are rejected with
+ * ISING_ERR_INVALID_ARG. Computes s = sign(x) (sign(0) = +1), E_r =
+ * -1/2 s_r^T J s_r and cut_r with W = -2J exactly in int64, as ising_energy.
+ *
+ * Its reduction partials live in a fixed device array inside the library
+ * (196,608 bytes, held on every device that loads the library until the
+ * process exits), so R is limited to 8192; larger R fails with
+ * ISING_ERR_INVALID_ARG. The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress, with the device current) and caches it;
+ * make that first call before any stream capture. Every call shares the
+ * array: two calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and may return wrong values. Work is
+ * enqueued on `stream` and not waited for.
+ */
+ISING_API ising_status_t ising_energy_torus_noalloc(const int8_t *right, const int8_t *down,
+                                                    int64_t l_rows, int64_t l_cols, const float *x,
+                                                    int32_t R, int64_t *E_out, int64_t *cut_out,
+                                                    void *stream);
+
+/*
  * Diagnostic: the FP32 cube root of the stencil kernel, sign(z) 2^(log2|z|/3)
  * evaluated on z 2^(-3k) and rescaled by 2^k, written to ours[i], next to
  * CUDA's cbrtf(z[i]) in ref[i]. z, ours, ref are device arrays of n floats;

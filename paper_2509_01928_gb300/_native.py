@@ -74,6 +74,9 @@ def load():
                                    ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
     lib.ising_synchronize.argtypes = [_vp, _vp]
     lib.ising_get_size.argtypes = [_vp, _vp, _vp]
+    lib.ising_energy_torus_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp,
+                                               ctypes.c_int32, _vp, _vp, _vp]
+    lib.ising_energy_torus_noalloc.restype = ctypes.c_int
     lib.ising_selftest_cbrt.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]
     lib.ising_selftest_cbrt.restype = ctypes.c_int
     lib.ising_status_string.argtypes = [ctypes.c_int]
@@ -259,6 +262,15 @@ def ising_backward(handle: int, x0, alpha, beta: float, iters: int, ckpt_every: 
                                  float(beta), int(ckpt_every), _ptr(grad_alpha), _ptr(grad_x0),
                                  _ptr(loss), _ptr(zero_events), _stream(stream, x0, grad_x0)),
            "ising_backward")
+
+
+def ising_energy_torus_noalloc(right, down, x, E_out=None, cut_out=None, stream=None):
+    """Lattice energy/cut from device arrays, with no device allocation (see include/ising.h)."""
+    lr, lc = int(right.shape[0]), int(right.shape[1])
+    R = 1 if x.ndim == 1 else int(x.shape[1])
+    _check(load().ising_energy_torus_noalloc(_ptr(right), _ptr(down), lr, lc, _ptr(x), R,
+                                             _ptr(E_out), _ptr(cut_out), _stream(stream, x)),
+           "ising_energy_torus_noalloc")
 
 
 def ising_synchronize(handle: int, stream=None):
