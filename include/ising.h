@@ -202,10 +202,17 @@ ISING_API ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t x
  *   g^N = -(1/R)(J x^N + h);  w^k = g^(k+1) / (3 (x^(k+1))^2) (0 where x^(k+1) = 0);
  *   dL/dalpha_k = sum w^k x^k / beta;  g^k = (J w^k + alpha_k w^k) / beta,
  * keeping x^(k) only every ckpt_every steps and recomputing each segment.
- *   x0       [n][R] F32 (CSR or TORUS2D, one instance).
- *   alpha    [iters] host array (the schedule); beta > 0 host scalar.
- *   grad_alpha  [iters] FP64;  grad_x0  [n][R] F32;  loss  FP64 scalar (all
- *            may be host or device; NULL skips an output).
+ *   x0       [n][R] F32 or F64 (CSR, one instance). The forward iterates
+ *            (checkpoints and recomputed segments) run in x0's precision; the
+ *            adjoint recursion runs in FP32 with FP64 reductions. d x^(k+1)/d x^k
+ *            contains 1/(3 (x^(k+1))^2), so components passing near zero in
+ *            the transient make the gradient sensitive to the trajectory: F64
+ *            gives gradients within ~1e-6 of the exact adjoint from any start,
+ *            F32 is exact to ~1e-5 only where the trajectory avoids such
+ *            crossings (e.g. from a converged state).
+ *   alpha    [iters] (the schedule); beta > 0 host scalar.
+ *   grad_alpha  [iters] FP64;  grad_x0  [n][R] of x0's type;  loss  FP64
+ *            scalar (all may be host or device; NULL skips an output).
  *   zero_events  int64 scalar or NULL: components where x^(k+1) was exactly 0.
  */
 ISING_API ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, int32_t R,

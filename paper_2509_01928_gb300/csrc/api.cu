@@ -729,9 +729,103 @@ ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int3
 ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, int32_t R, const double *alpha,
                               int32_t iters, double beta, int32_t ckpt_every, double *grad_alpha,
                               void *grad_x0, double *loss, int64_t *zero_events, void *stream) {
-    (void)h; (void)x0; (void)xtype; (void)R; (void)alpha; (void)iters; (void)beta; (void)ckpt_every;
-    (void)grad_alpha; (void)grad_x0; (void)loss; (void)zero_events; (void)stream;
-    return fail(ISING_ERR_UNSUPPORTED, "ising_backward is not built yet");
+    g_err.clear();
+    if (!h || !x0 || !alpha) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    ising_context *c = h;
+    if (c->format != ISING_FMT_CSR || c->n_inst != 1)
+        return fail(ISING_ERR_UNSUPPORTED, "ising_backward runs on one CSR instance");
+    if (xtype != ISING_F32 && xtype != ISING_F64)
+        return fail(ISING_ERR_INVALID_ARG, "ising_backward iterates are F32 or F64");
+    const size_t xel = xtype == ISING_F64 ? 8 : 4;
+    if (R < 1 || R > 65535 || iters < 1 || ckpt_every < 1)
+        return fail(ISING_ERR_INVALID_ARG, "need 1 <= R <= 65535, iters >= 1, ckpt_every >= 1");
+    if (!std::isfinite(beta) || beta <= 0.0) return fail(ISING_ERR_INVALID_ARG, "beta must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int C = ckpt_every < iters ? ckpt_every : iters;
+    const int S = (iters + C - 1) / C;                   // checkpoints x^(sC), s = 0..S-1
+    std::vector<double> alpha_h(iters);
+    {
+        std::vector<unsigned char> tmp;
+        DOCH_CHECK(to_host(alpha, sizeof(double) * iters, tmp));
+        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
+    }
+    ParamTabs p;
+    DOCH_CHECK(upload_params(c, alpha_h.data(), iters, &beta, p, st));
+    const int V = (R % 4 == 0) ? 4 : (R % 2 == 0 ? 2 : 1);
+    const int64_t work = c->n * (R / V);
+    int64_t grid64 = (work + 255) / 256;
+    if (grid64 > 8LL * c->num_sms) grid64 = 8LL * c->num_sms;
+    const int grid = static_cast<int>(grid64 < 1 ? 1 : grid64);
+    // layout of the handle's checkpoint buffer
+    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t A = al(static_cast<size_t>(c->n) * R * xel);        // one iterate
+    const size_t G = al(static_cast<size_t>(c->n) * R * sizeof(float)); // one adjoint state
+    const size_t part_b = al(sizeof(double) * static_cast<size_t>(iters) * grid);
+    const size_t lpart_b = al(sizeof(double) * grid);
+    const size_t out_b = al(sizeof(double) * (static_cast<size_t>(iters) + 1) + 8);
+    const size_t wide_b = xtype == ISING_F64 ? A : 0;                   // FP64 copy of dL/dx0
+    DOCH_CHECK(c->ckpt.ensure(A * (S + C) + 2 * G + wide_b + part_b + lpart_b + out_b));
+    unsigned char *base = c->ckpt.as<unsigned char>();
+    auto ck = [&](int sg_i) { return static_cast<void *>(base + A * sg_i); };
+    auto sg = [&](int m) { return static_cast<void *>(base + A * (S + m)); };
+    unsigned char *tail = base + A * (S + C);
+    float *gbuf[2] = {reinterpret_cast<float *>(tail), reinterpret_cast<float *>(tail + G)};
+    double *wide = reinterpret_cast<double *>(tail + 2 * G);
+    double *part = reinterpret_cast<double *>(tail + 2 * G + wide_b);
+    double *lpart = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b);
+    double *ga_d = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b + lpart_b);
+    double *loss_d = ga_d + iters;
+    unsigned long long *zeros_d = reinterpret_cast<unsigned long long *>(loss_d + 1);
+    DOCH_CUDA(cudaMemsetAsync(zeros_d, 0, 8, st));
+    const size_t xbytes = static_cast<size_t>(c->n) * R * xel;
+    DOCH_CUDA(cudaMemcpyAsync(ck(0), x0, xbytes, cudaMemcpyDefault, st));
+    // x^(sC + m) of segment s: checkpoint, recomputed iterate, or the next checkpoint
+    auto seg_len = [&](int sg_i) { return std::min(C, iters - sg_i * C); };
+    auto xs = [&](int sg_i, int m) -> void * {
+        if (m == 0) return ck(sg_i);
+        if (m == seg_len(sg_i) && sg_i + 1 < S) return ck(sg_i + 1);
+        return sg(m - 1);
+    };
+    // forward: all segments, storing the checkpoints
+    for (int sg_i = 0; sg_i < S; ++sg_i)
+        for (int m = 1; m <= seg_len(sg_i); ++m)
+            DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
+    // loss and g^N (x^N is the last iterate of the last segment)
+    int gc = 0;
+    DOCH_CHECK(csr_loss_grad(c, xs(S - 1, seg_len(S - 1)), xtype, gbuf[gc], R, V, grid, lpart, st));
+    const float inv_beta = static_cast<float>(1.0 / beta);
+    for (int sg_i = S - 1; sg_i >= 0; --sg_i) {
+        const int len = seg_len(sg_i);
+        if (sg_i < S - 1)  // the last segment's iterates are still in place from the forward pass
+            for (int m = 1; m < len; ++m)
+                DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
+        for (int m = len - 1; m >= 0; --m) {
+            const int k = sg_i * C + m;
+            DOCH_CHECK(csr_adjoint_step(c, gbuf[gc], xs(sg_i, m + 1), xs(sg_i, m), xtype, gbuf[1 - gc], R, V,
+                                        static_cast<float>(alpha_h[k]), inv_beta, grid,
+                                        part + static_cast<size_t>(k) * grid, zeros_d, st));
+            gc = 1 - gc;
+        }
+    }
+    DOCH_CHECK(adjoint_finish_launch(part, iters, grid, beta, lpart, grid, R, ga_d, loss_d, st));
+    bool must_sync = false;
+    auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
+        if (!dst) return ISING_OK;
+        if (!is_device_ptr(dst)) must_sync = true;
+        DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+        return ISING_OK;
+    };
+    if (xtype == ISING_F64) {
+        DOCH_CHECK(widen_f32_to_f64(gbuf[gc], wide, c->n * R, c->num_sms, st));
+        DOCH_CHECK(put(grad_x0, wide, xbytes));
+    } else {
+        DOCH_CHECK(put(grad_x0, gbuf[gc], xbytes));
+    }
+    DOCH_CHECK(put(grad_alpha, ga_d, sizeof(double) * iters));
+    DOCH_CHECK(put(loss, loss_d, sizeof(double)));
+    DOCH_CHECK(put(zero_events, zeros_d, sizeof(int64_t)));
+    if (!is_device_ptr(x0)) must_sync = true;
+    return finish(c, st, must_sync);
 }
 
 }  // extern "C"

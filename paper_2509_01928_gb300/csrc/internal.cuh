@@ -18,16 +18,18 @@ void set_error(const std::string &msg);
 ising_status_t fail(ising_status_t s, const std::string &msg);
 ising_status_t cuda_fail(cudaError_t e, const char *what);
 
-#define DOCH_CUDA(call)                                                  \
-    do {                                                                 \
-        cudaError_t e_ = (call);                                         \
-        if (e_ != cudaSuccess) return ::doch::cuda_fail(e_, #call);      \
+// (the locals carry a long prefix so that they cannot capture a name used in the argument)
+#define DOCH_CUDA(call)                                                          \
+    do {                                                                         \
+        cudaError_t doch_macro_err_ = (call);                                    \
+        if (doch_macro_err_ != cudaSuccess)                                      \
+            return ::doch::cuda_fail(doch_macro_err_, #call);                    \
     } while (0)
 
-#define DOCH_CHECK(st)                                                   \
-    do {                                                                 \
-        ising_status_t s_ = (st);                                        \
-        if (s_ != ISING_OK) return s_;                                   \
+#define DOCH_CHECK(expr)                                                         \
+    do {                                                                         \
+        ising_status_t doch_macro_status_ = (expr);                              \
+        if (doch_macro_status_ != ISING_OK) return doch_macro_status_;           \
     } while (0)
 
 // ---------------------------------------------------------------------------
@@ -48,6 +50,20 @@ struct Dims {
     int64_t n = 0;
     int n_inst = 1;
 };
+
+// Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
+// (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss
+// partials; one adjoint step; FP32 -> FP64 widening; the fixed-order finish.
+ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
+                             int grid, double *part, cudaStream_t st);
+ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
+                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
+                                float inv_beta, int grid, double *part, unsigned long long *zeros,
+                                cudaStream_t st);
+ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st);
+ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
+                                     const double *lpart, int lblocks, int R, double *grad_alpha,
+                                     double *loss, cudaStream_t st);
 
 }  // namespace doch
 
@@ -140,5 +156,19 @@ ising_status_t write_spins(const ising_context *c, const void *x, int xtype, int
 // alpha of step k is taken from the tables (k clamped to alpha_len - 1).
 ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, int R,
                                   const ParamTabs &p, int k, double *H_out, cudaStream_t st);
+
+// Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
+// (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss
+// partials; one adjoint step; FP32 -> FP64 widening; the fixed-order finish.
+ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
+                             int grid, double *part, cudaStream_t st);
+ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
+                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
+                                float inv_beta, int grid, double *part, unsigned long long *zeros,
+                                cudaStream_t st);
+ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st);
+ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
+                                     const double *lpart, int lblocks, int R, double *grad_alpha,
+                                     double *loss, cudaStream_t st);
 
 }  // namespace doch

@@ -1,0 +1,313 @@
+// Adjoint of N DOCH steps (derived from Eq. FPE; the paper has no gradients).
+//
+// Precision: the forward iterates (checkpoints and recomputed segments) are
+// FP32 or FP64 as the caller's x0; the adjoint recursion (g, w) runs in FP32.
+// The FP64 forward exists because d x^(k+1) / d x^k contains
+// 1 / (3 (x^(k+1))^2): components that pass near zero in the transient make
+// the gradient sensitive to the trajectory, and an FP32 trajectory shifts
+// those factors enough to move some gradients by 1e-3..1e-1 relative on
+// random regular graphs. Along an FP64 trajectory the FP32 adjoint is
+// accurate to ~1e-6.
+//
+// Loss: L = (1/R) sum_r ( -1/2 x_r^T J x_r - h^T x_r ) at x^N.
+//   g^N = dL/dx^N = -(1/R) (J x^N + h)
+//   for k = N-1 .. 0 (x^(k+1) = cbrt(z^k), dx^(k+1)/dz^k = 1 / (3 (x^(k+1))^2)):
+//     w^k = g^(k+1) / (3 (x^(k+1))^2)            (0 where x^(k+1) = 0, counted)
+//     dL/dalpha_k = sum_{i,r} w^k_ir x^k_ir / beta
+//     g^k = (J w^k + alpha_k w^k) / beta           (J = J^T)
+//   dL/dx^0 = g^0.
+//
+// Memory: x is kept only every C steps (checkpoints); each segment is
+// recomputed from its checkpoint with the forward kernel (deterministic, so
+// the recomputed iterates equal the forward ones) before its adjoint steps
+// run. One adjoint kernel per step forms w_j for every neighbour j on the fly
+// from g^(k+1) and x^(k+1), so w is never stored. dL/dalpha_k and the loss
+// are FP64 per-block partials summed in block order (run-to-run identical).
+//
+// Thread layout as in the forward CSR kernel: one thread per (row, chunk of
+// V = 4/2/1 replicas), grid-stride over a fixed grid.
+#include "internal.cuh"
+
+namespace doch {
+namespace {
+
+constexpr int kBThreads = 256;
+
+template <int V> struct F4;
+template <> struct F4<1> { using type = float; };
+template <> struct F4<2> { using type = float2; };
+template <> struct F4<4> { using type = float4; };
+
+template <int V>
+__device__ __forceinline__ void ld(const float *p, float (&v)[V]) {
+    using T = typename F4<V>::type;
+    const T w = __ldg(reinterpret_cast<const T *>(p));
+    const float *q = reinterpret_cast<const float *>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = q[k];
+}
+
+// FP64 iterates: loaded as doubles (two 16-byte loads for V = 4)
+template <int V>
+__device__ __forceinline__ void ld(const double *p, double (&v)[V]) {
+    if constexpr (V == 4) {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else if constexpr (V == 2) {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st(float *p, const float (&v)[V]) {
+    using T = typename F4<V>::type;
+    T w;
+    float *q = reinterpret_cast<float *>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) q[k] = v[k];
+    *reinterpret_cast<T *>(p) = w;
+}
+
+__device__ __forceinline__ float dcbrt_weight(float g, float x) {
+    return x == 0.0f ? 0.0f : g / (3.0f * x * x);
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double red[kBThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kBThreads / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// g = -(J x + h) / R (FP32) and per-block partial sums of -1/2 x u - h x (FP64);
+// the product u is formed in the iterate type XT
+template <typename XT, typename VT, int V>
+__global__ void __launch_bounds__(kBThreads)
+loss_grad_kernel(const XT *__restrict__ x, float *__restrict__ g, const int64_t *__restrict__ row_ptr,
+                 const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
+                 int64_t n, int R, double *__restrict__ part) {
+    const int C = R / V;
+    const XT invR = XT(1) / static_cast<XT>(R);
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(kBThreads) + threadIdx.x; t < n * C;
+         t += static_cast<int64_t>(gridDim.x) * kBThreads) {
+        const int64_t i = t / C;
+        const int ch = static_cast<int>(t - i * C);
+        XT u[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) u[q] = XT(0);
+        const int64_t e1 = __ldg(row_ptr + i + 1);
+        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
+            const XT w = static_cast<XT>(__ldg(val + e));
+            XT xv[V];
+            ld<V>(x + static_cast<int64_t>(__ldg(col + e)) * R + ch * V, xv);
+#pragma unroll
+            for (int q = 0; q < V; ++q) u[q] += w * xv[q];
+        }
+        XT xi[V];
+        float gi[V];
+        ld<V>(x + i * R + ch * V, xi);
+        const XT hi = h ? h[i] : XT(0);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            acc += -0.5 * static_cast<double>(xi[q]) * static_cast<double>(u[q]) -
+                   static_cast<double>(hi) * static_cast<double>(xi[q]);
+            gi[q] = static_cast<float>(-(u[q] + hi) * invR);
+        }
+        st<V>(g + i * R + ch * V, gi);
+    }
+    const double b = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+// one adjoint step: g_out = (J w + alpha_k w) / beta, w = g_in / (3 x_next^2);
+// iterates of type XT are rounded to FP32 for the adjoint arithmetic
+template <typename XT, typename VT, int V>
+__global__ void __launch_bounds__(kBThreads)
+adjoint_step_kernel(const float *__restrict__ g_in, const XT *__restrict__ x_next,
+                    const XT *__restrict__ x_cur, float *__restrict__ g_out,
+                    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                    const VT *__restrict__ val, int64_t n, int R, float alpha_k, float inv_beta,
+                    double *__restrict__ part, unsigned long long *__restrict__ zeros) {
+    const int C = R / V;
+    double ga = 0.0;
+    unsigned nz = 0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(kBThreads) + threadIdx.x; t < n * C;
+         t += static_cast<int64_t>(gridDim.x) * kBThreads) {
+        const int64_t i = t / C;
+        const int ch = static_cast<int>(t - i * C);
+        float acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = 0.f;
+        const int64_t e1 = __ldg(row_ptr + i + 1);
+        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
+            const int64_t j = __ldg(col + e);
+            const float w = static_cast<float>(__ldg(val + e));
+            float gj[V];
+            XT xj[V];
+            ld<V>(g_in + j * R + ch * V, gj);
+            ld<V>(x_next + j * R + ch * V, xj);
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += w * dcbrt_weight(gj[q], static_cast<float>(xj[q]));
+        }
+        float gi[V], out[V];
+        XT xn[V], xc[V];
+        ld<V>(g_in + i * R + ch * V, gi);
+        ld<V>(x_next + i * R + ch * V, xn);
+        ld<V>(x_cur + i * R + ch * V, xc);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const float wi = dcbrt_weight(gi[q], static_cast<float>(xn[q]));
+            nz += xn[q] == XT(0);
+            ga += static_cast<double>(wi) * static_cast<double>(xc[q]);
+            out[q] = (acc[q] + alpha_k * wi) * inv_beta;
+        }
+        st<V>(g_out + i * R + ch * V, out);
+    }
+    const double b = block_sum(ga);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    unsigned tot = nz;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(zeros, static_cast<unsigned long long>(tot));
+}
+
+// grad_alpha[k] = sum_b part[k][b] / beta (block order); loss = sum_b lpart[b] / R
+__global__ void adjoint_finish(const double *__restrict__ part, int iters, int blocks, double beta,
+                               const double *__restrict__ lpart, int lblocks, int R,
+                               double *__restrict__ grad_alpha, double *__restrict__ loss) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < iters) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += part[static_cast<int64_t>(k) * blocks + b];
+        grad_alpha[k] = s / beta;
+    }
+    if (k == 0) {
+        double s = 0.0;
+        for (int b = 0; b < lblocks; ++b) s += lpart[b];
+        *loss = s / R;
+    }
+}
+
+__global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t count) {
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        b[t] = a[t];
+}
+
+template <typename XT, typename VT, int V>
+void launch_loss(const ising_context *c, const XT *x, float *g, int R, int grid, double *part,
+                 cudaStream_t st) {
+    const XT *h = nullptr;
+    if constexpr (sizeof(XT) == 8) h = c->h_f64; else h = c->h_f32;
+    loss_grad_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(x, g, c->row_ptr, c->col,
+                                                            static_cast<const VT *>(c->val), h, c->n,
+                                                            R, part);
+}
+
+template <typename XT, typename VT, int V>
+void launch_adj(const ising_context *c, const float *gi, const XT *xn, const XT *xc, float *go,
+                int R, float a, float ib, int grid, double *part, unsigned long long *zeros,
+                cudaStream_t st) {
+    adjoint_step_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(gi, xn, xc, go, c->row_ptr, c->col,
+                                                               static_cast<const VT *>(c->val), c->n, R,
+                                                               a, ib, part, zeros);
+}
+
+template <typename XT, typename VT>
+ising_status_t loss_v(const ising_context *c, const XT *x, float *g, int R, int V, int grid,
+                      double *part, cudaStream_t st) {
+    if (V == 4) launch_loss<XT, VT, 4>(c, x, g, R, grid, part, st);
+    else if (V == 2) launch_loss<XT, VT, 2>(c, x, g, R, grid, part, st);
+    else launch_loss<XT, VT, 1>(c, x, g, R, grid, part, st);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+template <typename XT, typename VT>
+ising_status_t adj_v(const ising_context *c, const float *gi, const XT *xn, const XT *xc,
+                     float *go, int R, int V, float a, float ib, int grid, double *part,
+                     unsigned long long *zeros, cudaStream_t st) {
+    if (V == 4) launch_adj<XT, VT, 4>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
+    else if (V == 2) launch_adj<XT, VT, 2>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
+    else launch_adj<XT, VT, 1>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+template <typename XT>
+ising_status_t loss_t(const ising_context *c, const XT *x, float *g, int R, int V, int grid,
+                      double *part, cudaStream_t st) {
+    switch (c->jtype) {
+        case ISING_I8: return loss_v<XT, int8_t>(c, x, g, R, V, grid, part, st);
+        case ISING_I32: return loss_v<XT, int32_t>(c, x, g, R, V, grid, part, st);
+        case ISING_F32: return loss_v<XT, float>(c, x, g, R, V, grid, part, st);
+        case ISING_F64: return loss_v<XT, double>(c, x, g, R, V, grid, part, st);
+        default: return fail(ISING_ERR_UNSUPPORTED, "backward: coupling type");
+    }
+}
+
+template <typename XT>
+ising_status_t adj_t(const ising_context *c, const float *g_in, const XT *x_next, const XT *x_cur,
+                     float *g_out, int R, int V, float alpha_k, float inv_beta, int grid, double *part,
+                     unsigned long long *zeros, cudaStream_t st) {
+    switch (c->jtype) {
+        case ISING_I8: return adj_v<XT, int8_t>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        case ISING_I32: return adj_v<XT, int32_t>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        case ISING_F32: return adj_v<XT, float>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        case ISING_F64: return adj_v<XT, double>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        default: return fail(ISING_ERR_UNSUPPORTED, "backward: coupling type");
+    }
+}
+
+}  // namespace
+
+ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
+                             int grid, double *part, cudaStream_t st) {
+    if (xtype == ISING_F64) return loss_t<double>(c, static_cast<const double *>(x), g, R, V, grid, part, st);
+    return loss_t<float>(c, static_cast<const float *>(x), g, R, V, grid, part, st);
+}
+
+ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
+                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
+                                float inv_beta, int grid, double *part, unsigned long long *zeros,
+                                cudaStream_t st) {
+    if (xtype == ISING_F64)
+        return adj_t<double>(c, g_in, static_cast<const double *>(x_next), static_cast<const double *>(x_cur),
+                             g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+    return adj_t<float>(c, g_in, static_cast<const float *>(x_next), static_cast<const float *>(x_cur), g_out,
+                        R, V, alpha_k, inv_beta, grid, part, zeros, st);
+}
+
+ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st) {
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    if (blocks < 1) blocks = 1;
+    widen_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a, b, count);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
+                                     const double *lpart, int lblocks, int R, double *grad_alpha,
+                                     double *loss, cudaStream_t st) {
+    const int threads = 128;
+    const int nb = (iters > 0 ? iters : 1) + threads - 1;
+    adjoint_finish<<<nb / threads, threads, 0, st>>>(part, iters, blocks, beta, lpart, lblocks, R,
+                                                    grad_alpha, loss);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+}  // namespace doch
