@@ -222,8 +222,9 @@ ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem
         DOCH_CHECK(to_host(p->down, n, hp.down));
     } else if (p->format == ISING_FMT_DENSE) {
         if (!p->dense) return fail(ISING_ERR_INVALID_ARG, "dense array is NULL");
-        if (p->jtype != ISING_I8 && p->jtype != ISING_F32 && p->jtype != ISING_F64)
-            return fail(ISING_ERR_UNSUPPORTED, "DENSE couplings must be I8, F32 or F64");
+        if (p->jtype != ISING_I8 && p->jtype != ISING_I16 && p->jtype != ISING_I32)
+            return fail(ISING_ERR_UNSUPPORTED,
+                        "DENSE couplings must be integers (held exactly as BF16 for the tensor cores)");
         DOCH_CHECK(to_host(p->dense, jsz * n * n, hp.dense));
         if (validate) {
             for (int64_t i = 0; i < n; ++i) {
@@ -232,6 +233,8 @@ ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem
                 for (int64_t j = i + 1; j < n; ++j) {
                     const double a = value_at(hp.dense.data(), p->jtype, i * n + j);
                     const double c = value_at(hp.dense.data(), p->jtype, j * n + i);
+                    if (std::fabs(a) > 256.0)
+                        return fail(ISING_ERR_UNSUPPORTED, "DENSE couplings must satisfy |J_ij| <= 256 (exact in BF16)");
                     if (!std::isfinite(a)) return fail(ISING_ERR_NONFINITE, "non-finite coupling");
                     if (a != c) return fail(ISING_ERR_NOT_SYMMETRIC, "J_ij != J_ji");
                 }
@@ -423,8 +426,23 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
         DOCH_CHECK(upload(&c->right, hp.right.data(), hp.right.size()));
         DOCH_CHECK(upload(&c->down, hp.down.data(), hp.down.size()));
     } else {
-        DOCH_CHECK(upload(&c->dense, hp.dense.data(), hp.dense.size()));
-        c->dense_type = hp.jtype;
+        // BF16 copy with the leading dimension rounded up to 8 (16-byte rows for TMA)
+        const int64_t n = hp.n, ld = (n + 7) / 8 * 8;
+        std::vector<uint16_t> bf(static_cast<size_t>(n) * ld, 0);
+        long long jsum = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                const double v = value_at(hp.dense.data(), hp.jtype, i * n + j);
+                float f = static_cast<float>(v);
+                uint32_t u;
+                std::memcpy(&u, &f, 4);
+                bf[static_cast<size_t>(i) * ld + j] = static_cast<uint16_t>(u >> 16);  // exact: |v| <= 256 integer
+                jsum += static_cast<long long>(v);
+            }
+        DOCH_CHECK(upload(&c->dense, bf.data(), bf.size() * 2));
+        c->dense_type = ISING_BF16;
+        c->dense_ld = ld;
+        c->dense_jsum = jsum;
     }
     if (c->has_h) {
         std::vector<float> hf(hp.n);
@@ -631,7 +649,13 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
         Hd = c->work.as<double>();
     }
     bool done = false;
-    if (!H_trace && c->format == ISING_FMT_CSR && iters > 0) {
+    if (c->format == ISING_FMT_DENSE) {
+        if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for DENSE couplings");
+        if (c->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "DENSE runs one instance");
+        if (iters > 0) DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
+        done = true;
+    }
+    if (!done && !H_trace && c->format == ISING_FMT_CSR && iters > 0) {
         ising_status_t s = csr_fused(c, xd, xtype, R, p, iters, st);
         if (s == ISING_OK) done = true;
         else if (s != ISING_ERR_UNSUPPORTED) return s;
@@ -700,7 +724,10 @@ ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int3
     double *Ed = reinterpret_cast<double *>(Ci + pairs);
     double *Cd = Ed + pairs;
     int32_t *Bd = reinterpret_cast<int32_t *>(Cd + pairs);
-    DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
+    if (c->format == ISING_FMT_DENSE)
+        DOCH_CHECK(dense_energy(c, xd, xtype, R, Ei, Ci, Ed, Cd, st));
+    else
+        DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
     if (best) DOCH_CHECK(best_replica(c, c->integer ? Ei : nullptr, Ed, R, Bd, st));
     auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
         if (!dst) return ISING_OK;

@@ -51,6 +51,12 @@ struct Dims {
     int n_inst = 1;
 };
 
+// Dense couplings on the tcgen05 tensor cores (k_dense_tc.cu): BF16 iterates.
+ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,
+                             double beta, int iters, cudaStream_t st);
+ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
+                            double *E_d, double *cut_d, cudaStream_t st);
+
 // Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
 // (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss
 // partials; one adjoint step; FP32 -> FP64 widening; the fixed-order finish.
@@ -91,9 +97,12 @@ struct ising_context {
     // TORUS2D
     int64_t l_rows = 0, l_cols = 0;
     int8_t *right = nullptr, *down = nullptr;
-    // DENSE (+-1 held as FP8 E4M3 bytes; other values as BF16)
+    // DENSE: integer couplings held as BF16 [n][dense_ld] (exact for |J| <= 256),
+    // dense_ld = n rounded up to 8 (zero padded) for 16-byte TMA strides
     void *dense = nullptr;
     int dense_type = 0;
+    int64_t dense_ld = 0;
+    long long dense_jsum = 0;  // sum_ij J_ij, for the cut
     // field (both precisions; integer copy when integral)
     float *h_f32 = nullptr;
     double *h_f64 = nullptr;
@@ -156,6 +165,12 @@ ising_status_t write_spins(const ising_context *c, const void *x, int xtype, int
 // alpha of step k is taken from the tables (k clamped to alpha_len - 1).
 ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, int R,
                                   const ParamTabs &p, int k, double *H_out, cudaStream_t st);
+
+// Dense couplings on the tcgen05 tensor cores (k_dense_tc.cu): BF16 iterates.
+ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,
+                             double beta, int iters, cudaStream_t st);
+ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
+                            double *E_d, double *cut_d, cudaStream_t st);
 
 // Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
 // (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss

@@ -1,0 +1,488 @@
+// Dense coupling matrix on the tcgen05 tensor cores.
+//
+// One DOCH step (Eq. FPE) for dense J and R replicas is a GEMM followed by a
+// pointwise update:  U = J X  (n x n by n x R),  X' = cbrt((U + alpha X + h) / beta).
+// The energy readout is the same GEMM with the spins S = sign(X):
+// q_r = sum_i s_ir (J S)_ir, E_r = -q_r/2 - h^T s_r, cut_r = -(J_sum - q_r)/2
+// (Eq. IsingModel; Supplementary Note 5 with W = -2J). Integer J with |J| <= 256
+// is exact in BF16 and every (J S) entry is an integer below 2^24, so the FP32
+// accumulator and the int64 reduction are exact.
+//
+// Layout: J is BF16 [n_pad rows][ld] row-major (ld = n rounded up to 8,
+// zero padded); the iterate is held replica-major, Xt [R_pad][ld] BF16, so
+// both MMA operands are K-major. Tiles: one CTA per (128 rows of J) x
+// (N = up to 256 replicas).
+//
+// Pipeline per CTA (256 threads):
+//   warp 0, one lane: TMA producer. K-block kb (64 columns of J = 64 rows of
+//     X) goes to stage kb % kStages: A tile 128 x 64 (16 KB), B tile N x 64,
+//     both 128-byte swizzled; arrival tracked by the stage's "full" mbarrier.
+//   warp 1, one lane: MMA issuer. Waits "full", issues four
+//     tcgen05.mma.kind::f16 (K = 16 each) into the TMEM accumulator, and
+//     tcgen05.commit's the stage's "empty" mbarrier (the producer may reuse
+//     it once the MMAs that read it complete). After the last block it
+//     commits the "accumulator ready" mbarrier.
+//   warp 2: allocates and frees the TMEM columns.
+//   warps 4-7: epilogue. Warp 4+q owns TMEM lanes (rows) 32q..32q+31; it
+//     reads the accumulator 32 columns at a time (tcgen05.ld 32x32b.x32) and
+//     writes the new iterate (or the energy partials).
+// Every mbarrier wait is bounded (~1 s of %globaltimer); on expiry the CTA
+// sets the error word, drains its TMA copies (bounded), frees TMEM, returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace doch {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kBM = 128;           // rows of J per tile (MMA M)
+constexpr int kBK = 64;            // K per stage: 64 BF16 = 128 bytes = one swizzle row
+constexpr int kThreadsTC = 256;
+constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
+
+struct DenseSmem {
+    alignas(1024) unsigned char a[kStages][kBM * kBK * 2];
+    alignas(1024) unsigned char b[kStages][256 * kBK * 2];
+    alignas(8) unsigned long long full[kStages];
+    alignas(8) unsigned long long empty[kStages];
+    alignas(8) unsigned long long acc_ready;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on a phase parity; false (and the error word set) on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *err,
+                                          volatile int *abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtime() - t0 > kWaitNs) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+// K-major, 128-byte swizzled operand tile: rows are 128 bytes apart, groups of
+// 8 rows 1024 bytes apart (stride byte offset); descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *tile) {
+    const uint64_t start = (saddr(tile) & 0x3FFFFu) >> 4;
+    uint64_t d = start;
+    d |= static_cast<uint64_t>(1) << 16;           // leading byte offset (unused for swizzled K-major)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;   // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;           // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;           // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// MODE 0: DOCH step into Xt_out. MODE 1: energy partials q_r into q_out (int64).
+template <int MODE>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constant__ CUtensorMap tmap_x,
+                const __nv_bfloat16 *__restrict__ xt_in, __nv_bfloat16 *__restrict__ xt_out,
+                const float *__restrict__ h, int n, int ld, int R, int n_tile, uint32_t tmem_cols,
+                float alpha, float inv_beta, long long *__restrict__ q_out, int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM;
+    const int r0 = blockIdx.y * n_tile;
+    const int kblocks = (ld + kBK - 1) / kBK;
+    const uint32_t b_bytes = static_cast<uint32_t>(n_tile) * kBK * 2;
+    volatile int *abort_flag = &sm.abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], 1);
+        }
+        mbar_init(&sm.acc_ready, 1);
+        sm.abort_flag = 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sm.tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm.tmem_base;
+
+    int issued = 0;  // producer: K-blocks whose copies were issued
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % kStages;
+            if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) - 1) & 1, err, abort_flag)) break;
+            mbar_expect_tx(&sm.full[s], kBM * kBK * 2 + b_bytes);
+            tma_load_2d(sm.a[s], &tmap_j, kb * kBK, m0, &sm.full[s]);
+            tma_load_2d(sm.b[s], &tmap_x, kb * kBK, r0, &sm.full[s]);
+            issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16(kBM, n_tile);
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(&sm.full[s], (kb / kStages) & 1, err, abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ad = smem_desc_sw128(sm.a[s]);
+            const uint64_t bd = smem_desc_sw128(sm.b[s]);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)  // K = 16 per MMA: +32 bytes = +2 in the descriptor
+                mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+            mma_commit(&sm.empty[s]);
+        }
+        // the accumulator barrier also tracks completion of every MMA issued so far
+        mma_commit(&sm.acc_ready);
+        if (!ok) {  // error path: let the issued MMAs finish before TMEM is freed
+            const uint64_t t0 = gtime();
+            while (!mbar_test(&sm.acc_ready, 0) && gtime() - t0 < kWaitNs) {
+            }
+        }
+    } else if (warp >= 4) {
+        const int q = warp - 4;
+        const int row = m0 + 32 * q + lane;
+        // warp-uniform decision: tcgen05.ld below is a .sync.aligned warp instruction
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.acc_ready, 0, err, abort_flag) && !*abort_flag);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float hv = (h && row < n) ? h[row] : 0.f;
+            for (int c0 = 0; c0 < n_tile; c0 += 32) {
+                float acc[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + c0, acc);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const int r = r0 + c0 + k;
+                    if (MODE == 0) {
+                        if (row < n && r < R) {
+                            const size_t idx = static_cast<size_t>(r) * ld + row;
+                            const float xo = __bfloat162float(xt_in[idx]);
+                            const float z = (acc[k] + alpha * xo + hv) * inv_beta;
+                            xt_out[idx] = __float2bfloat16_rn(cbrtf(z));
+                        }
+                    } else {
+                        long long contrib = 0;
+                        if (row < n && r < R) {
+                            const float s = __bfloat162float(xt_in[static_cast<size_t>(r) * ld + row]);
+                            contrib = static_cast<long long>(s) * static_cast<long long>(acc[k]);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+                        if (lane == 0 && r < R && contrib != 0) atomicAdd(reinterpret_cast<unsigned long long *>(q_out + r),
+                                                                      static_cast<unsigned long long>(contrib));
+                    }
+                }
+            }
+        }
+    }
+    // drain: the producer waits (bounded) until every copy it issued has landed
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb) {
+            const uint64_t t0 = gtime();
+            while (!mbar_test(&sm.full[kb % kStages], (kb / kStages) & 1) && gtime() - t0 < kWaitNs) {
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// x [n][R] (caller layout, BF16) <-> Xt [R_pad][ld] (replica-major, zero padded)
+__global__ void to_replica_major(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, int n,
+                                 int R, int ld) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = i0 + k, r = r0 + threadIdx.x;
+        tile[k][threadIdx.x] = (i < n && r < R) ? x[static_cast<size_t>(i) * R + r] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, i = i0 + threadIdx.x;
+        if (r < R && i < n) xt[static_cast<size_t>(r) * ld + i] = tile[threadIdx.x][k];
+    }
+}
+
+__global__ void from_replica_major(const __nv_bfloat16 *__restrict__ xt, __nv_bfloat16 *__restrict__ x, int n,
+                                   int R, int ld) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, i = i0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < R && i < n) ? xt[static_cast<size_t>(r) * ld + i] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = i0 + k, r = r0 + threadIdx.x;
+        if (i < n && r < R) x[static_cast<size_t>(i) * R + r] = tile[threadIdx.x][k];
+    }
+}
+
+// spins (BF16 +1/-1, sign(0) = +1) of iterates of any supported type, replica-major
+template <typename XT>
+__global__ void spins_replica_major(const XT *__restrict__ x, __nv_bfloat16 *__restrict__ st, int n, int R,
+                                    int ld) {
+    const int64_t total = static_cast<int64_t>(n) * R;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = t / R;
+        const int r = static_cast<int>(t - i * R);
+        float v;
+        if constexpr (sizeof(XT) == 2) v = __bfloat162float(x[t]);
+        else v = static_cast<float>(x[t]);
+        st[static_cast<size_t>(r) * ld + i] = __float2bfloat16_rn(v >= 0.f ? 1.f : -1.f);
+    }
+}
+
+__global__ void field_dot_spins(const __nv_bfloat16 *__restrict__ st, const int64_t *__restrict__ h, int n,
+                                int ld, long long *__restrict__ hs) {
+    const int r = blockIdx.y;
+    long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc += h[i] * static_cast<long long>(__bfloat162float(st[static_cast<size_t>(r) * ld + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(hs + r),
+                                                  static_cast<unsigned long long>(acc));
+}
+
+__global__ void dense_energy_finish(const long long *__restrict__ q, const long long *__restrict__ hs,
+                                    long long j_sum, int R, int64_t *E_i, int64_t *cut_i, double *E_d,
+                                    double *cut_d) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const long long E = -(q[r] / 2) - hs[r];
+    const long long cut = -((j_sum - q[r]) / 2);
+    if (E_i) E_i[r] = E;
+    if (cut_i) cut_i[r] = cut;
+    if (E_d) E_d[r] = static_cast<double>(E);
+    if (cut_d) cut_d[r] = static_cast<double>(cut);
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+ising_status_t encode_fn(EncodeTiled *out) {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        DOCH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (!p || q != cudaDriverEntryPointSuccess)
+            return fail(ISING_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    *out = fn;
+    return ISING_OK;
+}
+
+// 2-D BF16 map over [rows][ld], box = 64 columns x box_rows rows, 128-byte swizzle
+ising_status_t make_map(CUtensorMap *map, const void *base, int ld, int rows, int box_rows) {
+    EncodeTiled enc;
+    DOCH_CHECK(encode_fn(&enc));
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ISING_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return ISING_OK;
+}
+
+struct DenseGeom {
+    int n, ld, R, R_pad, n_tile, m_tiles, r_tiles;
+    uint32_t tmem_cols;
+};
+
+DenseGeom geometry(const ising_context *c, int R) {
+    DenseGeom g;
+    g.n = static_cast<int>(c->n);
+    g.ld = static_cast<int>(c->dense_ld);
+    g.R = R;
+    g.R_pad = R <= 256 ? ((R + 15) / 16) * 16 : ((R + 255) / 256) * 256;
+    g.n_tile = g.R_pad < 256 ? g.R_pad : 256;
+    g.m_tiles = (g.n + kBM - 1) / kBM;
+    g.r_tiles = g.R_pad / g.n_tile;
+    uint32_t cols = 32;
+    while (cols < static_cast<uint32_t>(g.n_tile)) cols <<= 1;
+    g.tmem_cols = cols;
+    return g;
+}
+
+size_t smem_bytes() { return sizeof(DenseSmem) + 1024; }
+
+template <int MODE>
+ising_status_t launch_dense(const DenseGeom &g, const CUtensorMap &mj, const CUtensorMap &mx,
+                            const __nv_bfloat16 *xt_in, __nv_bfloat16 *xt_out, const float *h, float alpha,
+                            float inv_beta, long long *q_out, int *err, cudaStream_t st) {
+    auto kern = dense_tc_kernel<MODE>;
+    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes())));
+    dim3 grid(static_cast<unsigned>(g.m_tiles), static_cast<unsigned>(g.r_tiles));
+    kern<<<grid, kThreadsTC, smem_bytes(), st>>>(mj, mx, xt_in, xt_out, h, g.n, g.ld, g.R, g.n_tile, g.tmem_cols,
+                                                 alpha, inv_beta, q_out, err);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+}  // namespace
+
+ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,
+                             double beta, int iters, cudaStream_t st) {
+    const DenseGeom g = geometry(c, R);
+    const size_t xt_bytes = static_cast<size_t>(g.R_pad) * g.ld * 2;
+    DOCH_CHECK(c->work.ensure(2 * xt_bytes));
+    __nv_bfloat16 *xt[2] = {c->work.as<__nv_bfloat16>(),
+                            reinterpret_cast<__nv_bfloat16 *>(c->work.as<unsigned char>() + xt_bytes)};
+    DOCH_CUDA(cudaMemsetAsync(c->work.ptr, 0, 2 * xt_bytes, st));
+    dim3 tb(32, 8), tg((g.n + 31) / 32, (R + 31) / 32);
+    to_replica_major<<<tg, tb, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), xt[0], g.n, R, g.ld);
+    DOCH_CUDA(cudaGetLastError());
+    CUtensorMap mj, mx[2];
+    DOCH_CHECK(make_map(&mj, c->dense, g.ld, g.n, kBM));
+    DOCH_CHECK(make_map(&mx[0], xt[0], g.ld, g.R_pad, g.n_tile));
+    DOCH_CHECK(make_map(&mx[1], xt[1], g.ld, g.R_pad, g.n_tile));
+    const float inv_beta = static_cast<float>(1.0 / beta);
+    int cur = 0;
+    for (int k = 0; k < iters; ++k) {
+        const float a = static_cast<float>(alpha_h[alpha_len == 1 ? 0 : k]);
+        DOCH_CHECK(launch_dense<0>(g, mj, mx[cur], xt[cur], xt[1 - cur], c->h_f32, a, inv_beta, nullptr,
+                                   c->err_word, st));
+        cur = 1 - cur;
+    }
+    from_replica_major<<<tg, tb, 0, st>>>(xt[cur], static_cast<__nv_bfloat16 *>(x), g.n, R, g.ld);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
+                            double *E_d, double *cut_d, cudaStream_t st) {
+    const DenseGeom g = geometry(c, R);
+    const size_t st_bytes = static_cast<size_t>(g.R_pad) * g.ld * 2;
+    DOCH_CHECK(c->partials.ensure(st_bytes + 2 * sizeof(long long) * R + 256));
+    __nv_bfloat16 *sp = c->partials.as<__nv_bfloat16>();
+    long long *q = reinterpret_cast<long long *>(c->partials.as<unsigned char>() + ((st_bytes + 255) & ~size_t(255)));
+    long long *hs = q + R;
+    DOCH_CUDA(cudaMemsetAsync(c->partials.ptr, 0, c->partials.bytes, st));
+    const int64_t total = static_cast<int64_t>(g.n) * R;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 16LL * c->num_sms) blocks = 16LL * c->num_sms;
+    switch (xtype) {
+        case ISING_BF16: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), sp, g.n, R, g.ld); break;
+        case ISING_F32: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const float *>(x), sp, g.n, R, g.ld); break;
+        case ISING_F64: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const double *>(x), sp, g.n, R, g.ld); break;
+        case ISING_I8: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const int8_t *>(x), sp, g.n, R, g.ld); break;
+        default: return fail(ISING_ERR_INVALID_ARG, "dense energy: x type");
+    }
+    DOCH_CUDA(cudaGetLastError());
+    CUtensorMap mj, ms;
+    DOCH_CHECK(make_map(&mj, c->dense, g.ld, g.n, kBM));
+    DOCH_CHECK(make_map(&ms, sp, g.ld, g.R_pad, g.n_tile));
+    DOCH_CHECK(launch_dense<1>(g, mj, ms, sp, nullptr, nullptr, 0.f, 0.f, q, c->err_word, st));
+    if (c->h_i64) {
+        dim3 fg(static_cast<unsigned>((g.n + 255) / 256 < 64 ? (g.n + 255) / 256 : 64), static_cast<unsigned>(R));
+        field_dot_spins<<<fg, 256, 0, st>>>(sp, c->h_i64, g.n, g.ld, hs);
+        DOCH_CUDA(cudaGetLastError());
+    }
+    dense_energy_finish<<<(R + 127) / 128, 128, 0, st>>>(q, hs, c->dense_jsum, R, E_i, cut_i, E_d, cut_d);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+}  // namespace doch

@@ -69,10 +69,14 @@ def test_validation_rejects(lib, rows, status):
 
 
 def test_validation_rejects_nonfinite_and_bad_torus(lib):
-    J = np.array([[0.0, np.nan], [np.nan, 0.0]])
+    J = I.CSR(2, np.array([0, 1, 2]), np.array([1, 0], np.int32), np.array([np.nan, np.nan]))
     with pytest.raises(N.IsingError) as e:
         N.ising_default_params(N.Problem(J))
     assert e.value.name == "ISING_ERR_NONFINITE"
+    D = np.array([[0.0, 0.5], [0.5, 0.0]])     # real-valued dense J has no exact tensor-core form
+    with pytest.raises(N.IsingError) as e:
+        N.ising_default_params(N.Problem(D))
+    assert e.value.name == "ISING_ERR_UNSUPPORTED"
     t = I.Torus2D(np.ones((1, 4), np.int8), np.ones((1, 4), np.int8))
     with pytest.raises(N.IsingError) as e:
         N.ising_default_params(N.Problem(t))
