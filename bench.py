@@ -167,6 +167,391 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# workloads: one step = one pass of the whole hot path over one batch of input
+# ---------------------------------------------------------------------------
+
+class Torus:
+    """10^4 x 10^4 periodic lattice, FP32, R = 1, 500 iterations + readout (default)."""
+
+    dominant = DOMINANT
+    dtype = "f32"
+
+    def __init__(self, args, rank, N, I, torch):
+        self.L, self.iters, self.R = args.size, args.iters, 1
+        self.n = self.L * self.L
+        t = I.torus_pm1(self.L, self.L, seed=SEED + 1000 * rank)
+        self.x0 = I.x0_uniform(self.n, 1, seed=SEED + 1000 * rank)
+        prob = N.Problem(t)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.cut = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.best = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        self.launches = self.iters + 3
+        self.config = {"workload": f"torus2d {self.L}x{self.L} +-1 int8 couplings, FP32 iterates, R=1, "
+                                   f"{self.iters} DOCH iterations + sign + int64 energy/cut + best replica",
+                       "n": self.n, "replicas": 1, "iters": self.iters,
+                       "l2": "inputs larger than L2 (1.2 GB live per step); no flush",
+                       "alpha_beta": "Wigner estimate, eta = 1, beta of Eq. alphabeta"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, cut_int=self.cut, best=self.best, stream=sid)
+
+    def roofline(self, per_launch_s):
+        peak, kind = measured_peaks()
+        alg = BYTES_PER_SITE * self.n
+        ach = alg / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": recorded_traffic(), "kernel": self.dominant, "peak_kind": kind,
+                "algorithmic_bytes_per_launch": alg}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh_np = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        Eh, ch, bh = np.zeros(1, np.int64), np.zeros(1, np.int64), np.zeros(1, np.int32)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh_np, self.alpha, self.beta, self.iters, stream=sid)   # H2D x, D2H x
+            N.ising_energy(self.h, xh_np, E_int=Eh, cut_int=ch, best=bh, stream=sid)        # H2D x, D2H E
+        dt = time.perf_counter() - w0
+        return dt, 2 * self.n * 4, self.n * 4 + 8 + 8 + 4, \
+            "ising_iterate + ising_energy on pinned host arrays, each step continues from the last"
+
+    def cpu_baseline(self, args):
+        lr = lc = args.ref_size
+        u, dt = cpu_oracle_sample(lr, lc, args.cpu_iters)
+        return {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"torus {lr}x{lc} int8 +-1, {args.cpu_iters} FP64 DOCH iterations + sign + int64 energy"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+class Dense:
+    """Dense n = 16384, J = +-1 (BF16, exact), R = 256 BF16 replicas, 1000 iterations on tcgen05."""
+
+    dominant = "dense_tc_kernel"
+    dtype = "bf16"
+
+    def __init__(self, args, rank, N, I, torch):
+        self.n, self.R, self.iters = args.dense_n, 256, args.dense_iters
+        J = I.dense_pm1(self.n, seed=3 + 1000 * rank)
+        self.x0 = I.x0_uniform(self.n, self.R, seed=3 + 1000 * rank)
+        prob = N.Problem(J)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0_d = torch.from_numpy(self.x0).to(torch.bfloat16).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.cut = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.best = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        self.launches = self.iters + 2 + 4
+        self.config = {"workload": f"dense {self.n}x{self.n} +-1 (BF16, exact), R={self.R} BF16 replicas, "
+                                   f"{self.iters} DOCH iterations on tcgen05 + exact int64 energy/cut",
+                       "n": self.n, "replicas": self.R, "iters": self.iters,
+                       "l2": "J (537 MB) larger than L2; no flush"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, cut_int=self.cut, best=self.best, stream=sid)
+
+    def roofline(self, per_launch_s):
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
+        flops = 2.0 * self.n * self.n * self.R
+        ach = flops / per_launch_s / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": "measured (bf16 sustained)",
+                "algorithmic_flops_per_launch": flops}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh_np = self.x0_d.float().cpu().numpy()
+        xh = self.torch.from_numpy(xh_np).to(self.torch.bfloat16).pin_memory()
+        Eh = np.zeros(self.R, np.int64)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh, self.alpha, self.beta, self.iters, stream=sid)
+            N.ising_energy(self.h, xh, E_int=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 2
+        return dt, 2 * nb, nb + 8 * self.R, "ising_iterate + ising_energy on pinned host BF16 arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        n = 4096
+        J = I.dense_pm1(n, seed=3)
+        x0 = I.x0_uniform(n, 2, seed=3)
+        a, b = O.alpha_beta(J, 1.0, "wigner")
+        P = O.Problem(J)
+        t0 = time.perf_counter()
+        O.doch(P, x0, a, b, 2)
+        dt = time.perf_counter() - t0
+        return {"value": n * 2 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"dense {n}x{n} +-1, 2 replicas, 2 FP64 DOCH iterations"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+class Batched:
+    """512 uneven instances (n ~ U[500, 20000], d-regular d ~ U{3..10}, J ~ N(0,1) FP32,
+    h ~ N(0, 0.1)), R = 16, 2000 iterations in one persistent graph-captured launch."""
+
+    dominant = "batched_persistent"
+    dtype = "f32"
+
+    def __init__(self, args, rank, N, I, torch):
+        ns, ds = I.batched_sizes(args.batch_count, 500, 20000, 3, 10, seed=4 + 1000 * rank)
+        gs = [I.regular_gauss(int(n), int(d), seed=5000 + b + 100000 * rank) for b, (n, d) in enumerate(zip(ns, ds))]
+        hs = [I.field_gauss(g.n, 0.1, seed=7000 + b + 100000 * rank) for b, g in enumerate(gs)]
+        off = np.cumsum([0] + [g.n for g in gs]).astype(np.int64)
+        nz = np.cumsum([0] + [g.nnz for g in gs])
+        rp = np.concatenate([[0]] + [g.row_ptr[1:] + z for g, z in zip(gs, nz[:-1])])
+        col = np.concatenate([g.col + o for g, o in zip(gs, off[:-1])]).astype(np.int32)
+        val = np.concatenate([g.val for g in gs]).astype(np.float32)
+        self.nnz = int(nz[-1])
+        h = np.concatenate(hs).astype(np.float32)
+        self.n, self.R, self.iters, self.B = int(off[-1]), 16, args.batch_iters, len(gs)
+        prob = N.Problem(I.CSR(self.n, rp, col, val), h, off)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=0)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0 = I.x0_uniform(self.n, self.R, seed=4 + 1000 * rank)
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros((self.B, self.R), dtype=torch.float64, device="cuda")
+        self.best = torch.zeros(self.B, dtype=torch.int32, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = 1
+        self.launches = 1 + 3
+        self.config = {"workload": f"batched {self.B} instances, n in [500, 20000] (sum {self.n}), random "
+                                   f"d-regular d in 3..10, J ~ N(0,1) FP32, h ~ N(0,0.1), R={self.R}, "
+                                   f"{self.iters} iterations in one persistent graph-captured launch + FP64 energy",
+                       "n": self.n, "instances": self.B, "replicas": self.R, "iters": self.iters,
+                       "l2": "live set ~1.1 GB (> L2); per-instance state L2-resident during its run"}
+        # first call tunes the launch shape and captures the graph
+        self.x.copy_(self.x0_d)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, 4, n_instances=self.B)
+        N.ising_synchronize(self.h)
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid, n_instances=self.B)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_f64=self.E, best=self.best, stream=sid)
+
+    def roofline(self, per_launch_s):
+        peak, kind = measured_peaks()
+        # per iteration, streamed: col 4 B + val 4 B per entry, x read + write, h, row_ptr
+        per_iter = 8 * self.nnz + 2 * self.n * self.R * 4 + self.n * 4 + self.n * 8
+        alg = per_iter * self.iters
+        ach = alg / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": kind,
+                "algorithmic_bytes_per_launch": alg,
+                "note": "bytes of a streamed iteration; the kernel keeps each instance L2-resident, "
+                        "so a fraction above 1 measures the L2 reuse"}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        Eh = np.zeros((self.B, self.R))
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh, self.alpha, self.beta, self.iters, stream=sid, n_instances=self.B)
+            N.ising_energy(self.h, xh, E_f64=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 4
+        return dt, 2 * nb, nb + 8 * self.B * self.R, "ising_iterate + ising_energy on pinned host arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        g = I.regular_gauss(10000, 6, seed=5)
+        h = I.field_gauss(g.n, 0.1, seed=6)
+        x0 = I.x0_uniform(g.n, 16, seed=5)
+        a, b = O.alpha_beta(g, 1.0, "eig")
+        P = O.Problem(g, h)
+        t0 = time.perf_counter()
+        O.doch(P, x0, a, b, 200)
+        dt = time.perf_counter() - t0
+        return {"value": g.n * 16 * 200 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "one instance n = 10000, 6-regular, Gaussian J, h, R = 16, 200 FP64 iterations"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+class Backward:
+    """Adjoint: 3-regular n = 1e5, +-1, R = 64, 200 FP32 iterations, checkpoint every 20."""
+
+    dominant = "adjoint_step_kernel"
+    dtype = "f32"
+
+    def __init__(self, args, rank, N, I, torch):
+        g = I.regular_pm1(100000, 3, seed=5 + 1000 * rank)
+        self.n, self.R, self.iters, self.ckpt = g.n, 64, 200, 20
+        prob = N.Problem(g)
+        a, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
+        self.alpha = np.full(self.iters, a[0])
+        self.beta = float(self.beta[0])
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0 = I.x0_uniform(self.n, self.R, seed=5 + 1000 * rank)
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.ga = torch.zeros(self.iters, dtype=torch.float64, device="cuda")
+        self.gx = torch.zeros_like(self.x0_d)
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        self.launches = 3 * self.iters + 4
+        self.config = {"workload": f"adjoint: random 3-regular n=1e5 +-1, R=64, {self.iters} FP32 iterations, "
+                                   f"checkpoint every {self.ckpt}: loss + dL/dalpha[200] + dL/dx0",
+                       "n": self.n, "replicas": self.R, "iters": self.iters,
+                       "metric_note": "forward spin-updates per second of the whole gradient computation "
+                                      "(forward, recompute and adjoint)",
+                       "l2": "x 25.6 MB L2-resident"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        if ev_a is not None:
+            ev_a.record(stream)
+        self.N.ising_backward(self.h, self.x0_d, self.alpha, self.beta, self.iters, self.ckpt,
+                              grad_alpha=self.ga, grad_x0=self.gx, loss=self.loss, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+
+    def roofline(self, per_launch_s):
+        # whole call / 3 x iters launches: average launch of the forward, recompute and adjoint steps
+        return None
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        ga = np.zeros(self.iters)
+        gx = np.zeros_like(self.x0)
+        loss = np.zeros(1)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_backward(self.h, xh, self.alpha, self.beta, self.iters, self.ckpt, grad_alpha=ga,
+                             grad_x0=gx, loss=loss, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 4
+        return dt, nb, nb + 8 * (self.iters + 1), "ising_backward on pinned host x0, host gradients"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        g = I.regular_pm1(100000, 3, seed=5)
+        x0 = I.x0_uniform(g.n, 2, seed=5)
+        a, b = O.alpha_beta(g, 1.0, "wigner")
+        t0 = time.perf_counter()
+        O.backward(O.Problem(g), x0, np.full(self.iters, a), b, self.iters)
+        dt = time.perf_counter() - t0
+        return {"value": g.n * 2 * self.iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"adjoint of {self.iters} FP64 steps, n = 1e5 3-regular, 2 replicas"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+class Er800:
+    """Plain method, FP64: Erdos-Renyi n = 800, p = 0.06, +-1, R = 8, 1000 iterations."""
+
+    dominant = "csr_fused_kernel"
+    dtype = "f64"
+
+    def __init__(self, args, rank, N, I, torch):
+        g = I.erdos_renyi_pm1(800, 0.06, seed=1 + 1000 * rank)
+        self.n, self.R, self.iters = g.n, 8, 1000
+        prob = N.Problem(g)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=1)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0 = I.x0_uniform(self.n, self.R, seed=2 + 1000 * rank, dtype=np.float64)
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.cut = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.best = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = 1
+        self.launches = 1 + 3
+        self.config = {"workload": "plain method FP64: Erdos-Renyi n=800 p=0.06 +-1, R=8, 1000 iterations "
+                                   "(one launch, iterate in shared memory) + int64 energy/cut + best replica",
+                       "n": self.n, "replicas": self.R, "iters": self.iters, "l2": "on-chip problem"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, cut_int=self.cut, best=self.best, stream=sid)
+
+    def roofline(self, per_launch_s):
+        return None
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.x0.copy()
+        Eh = np.zeros(self.R, np.int64)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh, self.alpha, self.beta, self.iters, stream=sid)
+            N.ising_energy(self.h, xh, E_int=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 8
+        return dt, 2 * nb, nb + 8 * self.R, "ising_iterate + ising_energy on host arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        g = I.erdos_renyi_pm1(800, 0.06, seed=1)
+        x0 = I.x0_uniform(g.n, 8, seed=2, dtype=np.float64)
+        a, b = O.alpha_beta(g, 1.0, "eig")
+        t0 = time.perf_counter()
+        O.doch(O.Problem(g), x0, a, b, 1000)
+        dt = time.perf_counter() - t0
+        return {"value": g.n * 8 * 1000 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "the whole workload: n = 800, R = 8, 1000 FP64 iterations"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -185,36 +570,13 @@ def run_ours(args):
         dist.barrier()
     N.load()
 
-    L = args.size
-    iters = args.iters
-    R = 1
-    n = L * L
-    t = I.torus_pm1(L, L, seed=SEED + 1000 * rank)
-    x0 = I.x0_uniform(n, R, seed=SEED + 1000 * rank)
-    prob = N.Problem(t)
-    alpha, beta = N.ising_default_params(prob, eta=1.0, method=2)
-    handle = N.ising_create(prob, flags=N.FLAG_ASYNC)
-    del t
+    wl = WORKLOADS[args.workload](args, rank, N, I, torch)
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
-    x0_d = torch.from_numpy(x0).cuda()
-    x = torch.empty_like(x0_d)
-    E = torch.zeros(1, dtype=torch.int64, device="cuda")
-    cut = torch.zeros(1, dtype=torch.int64, device="cuda")
-    best = torch.zeros(1, dtype=torch.int32, device="cuda")
-
-    def step(ev_a=None, ev_b=None):
-        x.copy_(x0_d)
-        if ev_a is not None:
-            ev_a.record(stream)
-        N.ising_iterate(handle, x, alpha, beta, iters, stream=sid)
-        if ev_b is not None:
-            ev_b.record(stream)
-        N.ising_energy(handle, x, E_int=E, cut_int=cut, best=best, stream=sid)
 
     for _ in range(args.warmup):
-        step()
-    N.ising_synchronize(handle, sid)
+        wl.step(sid, stream)
+    N.ising_synchronize(wl.h, sid)
 
     gpu_id = None
     try:
@@ -233,80 +595,55 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_start.record(stream)
     for k in range(args.steps):
-        step(*evs[k])
+        wl.step(sid, stream, *evs[k])
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    N.ising_synchronize(handle, sid)
+    N.ising_synchronize(wl.h, sid)
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    iter_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    dom_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
     if world > 1:
-        tt = torch.tensor([elapsed, iter_s], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([elapsed, dom_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed, iter_s = tt.tolist()
-    updates = float(n) * R * iters * args.steps * world
-    value = updates / elapsed
+        elapsed, dom_s = tt.tolist()
+    value = wl.units * args.steps * world / elapsed
 
     # end to end through the C ABI with pinned host buffers
-    xh = torch.from_numpy(x0.copy()).pin_memory()
-    Eh = np.zeros(1, np.int64)
-    ch = np.zeros(1, np.int64)
-    bh = np.zeros(1, np.int32)
-    xh_np = xh.numpy()
     n_e2e = max(1, min(args.steps, 3))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(n_e2e):
-        N.ising_iterate(handle, xh_np, alpha, beta, iters, stream=sid)      # H2D x, D2H x
-        N.ising_energy(handle, xh_np, E_int=Eh, cut_int=ch, best=bh, stream=sid)  # H2D x, D2H E
-    e2e_t = time.perf_counter() - w0
+    e2e_t, h2d, d2h, how = wl.e2e(n_e2e, sid)
     if world > 1:
         tt = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_t = tt.item()
-    e2e_val = float(n) * R * iters * n_e2e * world / e2e_t
-    N.ising_destroy(handle)
+    e2e_val = wl.units * n_e2e * world / e2e_t
+    wl.close()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    peak, peak_kind = measured_peaks()
-    per_launch_s = iter_s / (args.steps * iters)
-    alg_bytes = BYTES_PER_SITE * n
-    achieved = alg_bytes / per_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(),
-                "kernel": DOMINANT, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": alg_bytes}
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        lr = lc = args.ref_size
-        u, dt = cpu_oracle_sample(lr, lc, args.cpu_iters)
-        cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"torus {lr}x{lc} int8 +-1, {args.cpu_iters} FP64 DOCH iterations + sign + int64 energy"}
+    per_launch_s = dom_s / (args.steps * wl.dominant_launches)
+    roofline = wl.roofline(per_launch_s)
+    cpu = wl.cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
+    config = dict(wl.config)
+    config["parallelism"] = f"replicas-only x{world}"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
-        "config": {"workload": f"torus2d {L}x{L} +-1 int8 couplings, FP32 iterates, R={R}, "
-                               f"{iters} DOCH iterations + sign + int64 energy/cut + best replica",
-                   "n": n, "replicas": R, "iters": iters, "parallelism": f"replicas-only x{world}",
-                   "l2": "inputs larger than L2 (1.2 GB live per step); no flush",
-                   "alpha_beta": "Wigner estimate, eta = 1, beta of Eq. alphabeta"},
-        "gpu_launches": args.steps * (iters + 3),
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
-                "d2h_bytes_per_step": n * 4 + 8 + 8 + 4,
-                "how": "ising_iterate + ising_energy on pinned host arrays, each step continues from the last"},
+        "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64)",
+        "config": config,
+        "gpu_launches": args.steps * wl.launches,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "how": how},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "iterate_ms_per_step": 1e3 * iter_s / args.steps,
+        "dominant_ms_per_step": 1e3 * dom_s / args.steps,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -325,6 +662,13 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=24, help="oracle iterations per reference step")
     ap.add_argument("--cpu-iters", type=int, default=96, help="oracle iterations of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="torus", choices=sorted(WORKLOADS),
+                    help="torus (default: 10^4 x 10^4 lattice), dense (16384 x 256 on tcgen05), "
+                         "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64)")
+    ap.add_argument("--dense-n", type=int, default=16384)
+    ap.add_argument("--dense-iters", type=int, default=1000)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-iters", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

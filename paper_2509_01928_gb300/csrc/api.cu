@@ -382,6 +382,10 @@ void destroy_ctx(ising_context *c) {
     cudaFree(c->h_i64);
     cudaFree(c->err_word);
     if (c->err_host) cudaFreeHost(c->err_host);
+    cudaFree(c->batch_order);
+    cudaFree(c->batch_queue);
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->ping.release();
     c->stage_x.release();
     c->stage_out.release();
@@ -406,6 +410,19 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
     c->has_h = !hp.h.empty();
     c->integer = dtype_integer(hp.jtype) && (!c->has_h || dtype_integer(hp.htype));
     DOCH_CHECK(upload(&c->inst_off, hp.off.data(), sizeof(int64_t) * hp.off.size()));
+    if (hp.format == ISING_FMT_CSR && hp.n_inst > 1) {
+        // longest-first queue order for the persistent batched kernel
+        std::vector<int64_t> work(hp.n_inst);
+        for (int b = 0; b < hp.n_inst; ++b)
+            work[b] = (hp.off[b + 1] - hp.off[b]) + (hp.row_ptr[hp.off[b + 1]] - hp.row_ptr[hp.off[b]]);
+        std::vector<int32_t> order(hp.n_inst);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+        DOCH_CHECK(upload(&c->batch_order, order.data(), sizeof(int32_t) * order.size()));
+        void *qp = nullptr;
+        DOCH_CUDA(cudaMalloc(&qp, sizeof(int)));
+        c->batch_queue = static_cast<int *>(qp);
+    }
     if (hp.format == ISING_FMT_CSR) {
         c->nnz = hp.row_ptr.back();
         for (int64_t i = 0; i < hp.n; ++i)
@@ -519,6 +536,109 @@ ising_status_t step(ising_context *c, const void *xi, void *xo, int xtype, int R
     }
     if (c->format == ISING_FMT_CSR) return csr_step(c, xi, xo, xtype, R, p, k, st);
     return fail(ISING_ERR_UNSUPPORTED, "this storage form has no iteration kernel yet");
+}
+
+
+// Autotuner for the batched persistent kernel: times each candidate shape for
+// a few steps on scratch copies of x and keeps the fastest, per R.
+ising_status_t tune_batched(ising_context *c, const float *x, int R, const ParamTabs &p, cudaStream_t st,
+                            BatchedConfig *out) {
+    auto it = c->batch_tuned.find(R);
+    if (it != c->batch_tuned.end()) {
+        *out = it->second;
+        return ISING_OK;
+    }
+    const size_t xbytes = static_cast<size_t>(c->n) * R * sizeof(float);
+    DOCH_CHECK(c->work.ensure(2 * xbytes));
+    float *ta = c->work.as<float>();
+    float *tb = reinterpret_cast<float *>(c->work.as<unsigned char>() + xbytes);
+    std::vector<BatchedConfig> cand;
+    for (int threads : {256, 512, 1024})
+        for (int vec : {4, 2, 1}) {
+            if (R % vec) continue;
+            for (int cps : {1, 2, 4}) {
+                if (threads * cps > 2048) continue;
+                BatchedConfig k;
+                k.threads = threads;
+                k.vec = vec;
+                k.ctas_per_sm = cps;
+                cand.push_back(k);
+            }
+        }
+    cudaEvent_t e0, e1;
+    DOCH_CUDA(cudaEventCreate(&e0));
+    DOCH_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    BatchedConfig best = cand.front();
+    const int probe = 8;
+    bool any = false;
+    for (const BatchedConfig &k : cand) {
+        DOCH_CUDA(cudaMemcpyAsync(ta, x, xbytes, cudaMemcpyDeviceToDevice, st));
+        const ising_status_t ws = batched_launch(c, k, ta, tb, R, p, 2, st);  // warm-up
+        if (ws == ISING_ERR_UNSUPPORTED) continue;                              // shape not launchable
+        DOCH_CHECK(ws);
+        any = true;
+        DOCH_CUDA(cudaEventRecord(e0, st));
+        DOCH_CHECK(batched_launch(c, k, ta, tb, R, p, probe, st));
+        DOCH_CUDA(cudaEventRecord(e1, st));
+        DOCH_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DOCH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!any) return fail(ISING_ERR_CUDA, "batched: no launchable shape");
+    g_err.clear();
+    c->batch_tuned[R] = best;
+    *out = best;
+    return ISING_OK;
+}
+
+// All steps of all instances: one persistent launch, captured once into a
+// CUDA graph (queue reset + kernel [+ copy back]) and replayed while the
+// buffers, parameters and shape stay the same.
+ising_status_t batched_iterate(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
+                               cudaStream_t st) {
+    BatchedConfig cfg;
+    DOCH_CHECK(tune_batched(c, x, R, p, st, &cfg));
+    const size_t xbytes = static_cast<size_t>(c->n) * R * sizeof(float);
+    DOCH_CHECK(c->ping.ensure(xbytes));
+    float *xb = c->ping.as<float>();
+    const std::vector<uintptr_t> key = {reinterpret_cast<uintptr_t>(x), reinterpret_cast<uintptr_t>(xb),
+                                        static_cast<uintptr_t>(R), static_cast<uintptr_t>(iters),
+                                        static_cast<uintptr_t>(p.alpha_len), reinterpret_cast<uintptr_t>(p.alpha_f),
+                                        reinterpret_cast<uintptr_t>(p.inv_beta_f), static_cast<uintptr_t>(cfg.threads),
+                                        static_cast<uintptr_t>(cfg.vec), static_cast<uintptr_t>(cfg.ctas_per_sm)};
+    if (!c->batch_exec || c->batch_key != key) {
+        if (c->batch_exec) {
+            cudaGraphExecDestroy(c->batch_exec);
+            c->batch_exec = nullptr;
+        }
+        if (!c->cap_stream) DOCH_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        DOCH_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        ising_status_t s = batched_launch(c, cfg, x, xb, R, p, iters, c->cap_stream);
+        if (s == ISING_OK && (iters & 1)) {
+            const cudaError_t e = cudaMemcpyAsync(x, xb, xbytes, cudaMemcpyDeviceToDevice, c->cap_stream);
+            if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync (capture)");
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (s != ISING_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        DOCH_CUDA(ee);
+        const cudaError_t ei = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        DOCH_CUDA(ei);
+        c->batch_key = key;
+    }
+    DOCH_CUDA(cudaGraphLaunch(c->batch_exec, st));
+    return ISING_OK;
 }
 
 }  // namespace
@@ -655,6 +775,10 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
         if (iters > 0) DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
         done = true;
     }
+    if (!done && !H_trace && c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && iters > 0) {
+        DOCH_CHECK(batched_iterate(c, static_cast<float *>(xd), R, p, iters, st));
+        done = true;
+    }
     if (!done && !H_trace && c->format == ISING_FMT_CSR && iters > 0) {
         ising_status_t s = csr_fused(c, xd, xtype, R, p, iters, st);
         if (s == ISING_OK) done = true;
@@ -779,8 +903,9 @@ ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, i
     ParamTabs p;
     DOCH_CHECK(upload_params(c, alpha_h.data(), iters, &beta, p, st));
     const int V = (R % 4 == 0) ? 4 : (R % 2 == 0 ? 2 : 1);
-    const int64_t work = c->n * (R / V);
-    int64_t grid64 = (work + 255) / 256;
+    if (R / V > 256) return fail(ISING_ERR_UNSUPPORTED, "ising_backward: R / vector width must be <= 256");
+    const int64_t rows_per_block = 256 / (R / V);
+    int64_t grid64 = (c->n + rows_per_block - 1) / rows_per_block;
     if (grid64 > 8LL * c->num_sms) grid64 = 8LL * c->num_sms;
     const int grid = static_cast<int>(grid64 < 1 ? 1 : grid64);
     // layout of the handle's checkpoint buffer

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,30 +47,12 @@ struct DevBuf {
 // device-side error word: bit 0 = a bounded wait ran out
 enum { DEV_ERR_TIMEOUT = 1 };
 
-struct Dims {
-    int64_t n = 0;
-    int n_inst = 1;
+// launch shape of the batched persistent kernel (picked by the autotuner)
+struct BatchedConfig {
+    int threads = 512;
+    int vec = 4;
+    int ctas_per_sm = 2;
 };
-
-// Dense couplings on the tcgen05 tensor cores (k_dense_tc.cu): BF16 iterates.
-ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,
-                             double beta, int iters, cudaStream_t st);
-ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
-                            double *E_d, double *cut_d, cudaStream_t st);
-
-// Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
-// (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss
-// partials; one adjoint step; FP32 -> FP64 widening; the fixed-order finish.
-ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
-                             int grid, double *part, cudaStream_t st);
-ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
-                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
-                                float inv_beta, int grid, double *part, unsigned long long *zeros,
-                                cudaStream_t st);
-ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st);
-ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
-                                     const double *lpart, int lblocks, int R, double *grad_alpha,
-                                     double *loss, cudaStream_t st);
 
 }  // namespace doch
 
@@ -107,7 +90,6 @@ struct ising_context {
     float *h_f32 = nullptr;
     double *h_f64 = nullptr;
     int64_t *h_i64 = nullptr;
-    // sums used by the cut identity
     // scratch
     doch::DevBuf ping;      // second iterate buffer for the Jacobi ping-pong
     doch::DevBuf stage_x;   // staging of host iterates
@@ -118,6 +100,14 @@ struct ising_context {
     doch::DevBuf work;      // misc. work space
     int *err_word = nullptr;  // device error word
     int *err_host = nullptr;  // pinned mirror
+    // batched instances: longest-first queue order, queue counter, tuned shapes,
+    // and the captured graph of the persistent launch with the key it was built for
+    int32_t *batch_order = nullptr;
+    int *batch_queue = nullptr;
+    std::map<int, doch::BatchedConfig> batch_tuned;  // by R
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<uintptr_t> batch_key;
 };
 
 namespace doch {
@@ -165,6 +155,11 @@ ising_status_t write_spins(const ising_context *c, const void *x, int xtype, int
 // alpha of step k is taken from the tables (k clamped to alpha_len - 1).
 ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, int R,
                                   const ParamTabs &p, int k, double *H_out, cudaStream_t st);
+
+// Batched persistent kernel (k_batched.cu): FP32 iterates, ping-pong xa <-> xb;
+// after `iters` steps the result is in xa (iters even) or xb (odd).
+ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
+                              const ParamTabs &p, int iters, cudaStream_t st);
 
 // Dense couplings on the tcgen05 tensor cores (k_dense_tc.cu): BF16 iterates.
 ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,

@@ -100,10 +100,11 @@ loss_grad_kernel(const XT *__restrict__ x, float *__restrict__ g, const int64_t 
     const int C = R / V;
     const XT invR = XT(1) / static_cast<XT>(R);
     double acc = 0.0;
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(kBThreads) + threadIdx.x; t < n * C;
-         t += static_cast<int64_t>(gridDim.x) * kBThreads) {
-        const int64_t i = t / C;
-        const int ch = static_cast<int>(t - i * C);
+    const int rows_per_block = kBThreads / C;
+    const int ch = threadIdx.x % C;
+    const int rl = threadIdx.x / C;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; rl < rows_per_block && i < n;
+         i += static_cast<int64_t>(gridDim.x) * rows_per_block) {
         XT u[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) u[q] = XT(0);
@@ -143,10 +144,11 @@ adjoint_step_kernel(const float *__restrict__ g_in, const XT *__restrict__ x_nex
     const int C = R / V;
     double ga = 0.0;
     unsigned nz = 0;
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(kBThreads) + threadIdx.x; t < n * C;
-         t += static_cast<int64_t>(gridDim.x) * kBThreads) {
-        const int64_t i = t / C;
-        const int ch = static_cast<int>(t - i * C);
+    const int rows_per_block = kBThreads / C;
+    const int ch = threadIdx.x % C;
+    const int rl = threadIdx.x / C;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; rl < rows_per_block && i < n;
+         i += static_cast<int64_t>(gridDim.x) * rows_per_block) {
         float acc[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) acc[q] = 0.f;

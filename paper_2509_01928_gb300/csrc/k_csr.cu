@@ -72,12 +72,14 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
                 const XT *__restrict__ alpha_tab, int alpha_len, int k,
                 const XT *__restrict__ beta_tab) {
     const int C = R / V;
-    const int64_t total = n * C;
     const int ak = alpha_len == 1 ? 0 : k;
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = t / C;
-        const int ch = static_cast<int>(t - i * C);
+    // each thread keeps one replica chunk and strides over rows: no division in the loop
+    const int rows_per_block = blockDim.x / C;
+    const int ch = threadIdx.x % C;
+    const int rl = threadIdx.x / C;
+    if (rl >= rows_per_block) return;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; i < n;
+         i += static_cast<int64_t>(gridDim.x) * rows_per_block) {
         const int b = n_inst > 1 ? find_inst(inst_off, n_inst, i) : 0;
         const XT a = alpha_tab[static_cast<int64_t>(b) * alpha_len + ak];
         const XT bb = beta_tab[b];
@@ -142,12 +144,14 @@ csr_fused_kernel(XT *__restrict__ x, const int64_t *__restrict__ row_ptr,
 template <typename XT, typename VT, int V>
 void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
                  const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, cudaStream_t st) {
-    const int64_t total = c->n * (R / V);
-    int64_t blocks = (total + 255) / 256;
+    const int C = R / V;
+    const int rows_per_block = C <= 256 ? 256 / C : 1;
+    int64_t blocks = (c->n + rows_per_block - 1) / rows_per_block;
     const int64_t cap = static_cast<int64_t>(c->num_sms) * 32;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    csr_step_kernel<XT, VT, V><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+    const int threads = C <= 256 ? 256 : ((C + 31) / 32) * 32;
+    csr_step_kernel<XT, VT, V><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
         xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
         c->n, R, alpha_tab, alpha_len, k, beta_tab);
 }
@@ -156,6 +160,7 @@ template <typename XT, int V>
 ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
                             const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab,
                             cudaStream_t st) {
+    if (R / V > 1024) return fail(ISING_ERR_UNSUPPORTED, "CSR step: R / vector width must be <= 1024");
     switch (c->jtype) {
         case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
         case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;

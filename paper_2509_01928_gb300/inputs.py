@@ -18,6 +18,8 @@ starting points x0 in [-1, 1).
 """
 from __future__ import annotations
 
+import collections
+
 import numpy as np
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -223,16 +225,15 @@ def random_regular(n: int, d: int, seed: int):
     b = np.maximum(e[:, 0], e[:, 1])
     m = a.size
     key = a * n + b
-    counts: dict = {}
-    for k in key.tolist():
-        counts[k] = counts.get(k, 0) + 1
+    counts = collections.Counter(key.tolist())
 
     def bad(idx):
         return a[idx] == b[idx] or counts[int(a[idx] * n + b[idx])] > 1
 
     rs = stream_seed(seed, TAG_REPAIR)
     draw = 0
-    todo = [t for t in range(m) if bad(t)]
+    _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+    todo = np.nonzero((a == b) | (cnt[inv] > 1))[0].tolist()
     guard = 0
     while todo:
         t = todo.pop()
