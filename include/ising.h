@@ -86,8 +86,10 @@ enum {
     ISING_FLAG_ASYNC = 1,            /* do not synchronise inside calls on device arrays */
     ISING_FLAG_SKIP_VALIDATION = 2,  /* skip the symmetry, diagonal and finiteness checks of
                                         J and h (index and size checks always run)        */
-    ISING_FLAG_STRICT_MONOTONE = 4   /* ising_iterate fails with ISING_ERR_NOT_MONOTONE
+    ISING_FLAG_STRICT_MONOTONE = 4,  /* ising_iterate fails with ISING_ERR_NOT_MONOTONE
                                         when a recorded H trace rises                    */
+    ISING_FLAG_SINGLE_STEP = 8       /* TORUS2D: one kernel pass per step instead of the
+                                        fused two-step pass (same results, more traffic) */
 };
 
 /*

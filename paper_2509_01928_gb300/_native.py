@@ -26,7 +26,7 @@ STATUS_NAMES = {
 }
 FMT_CSR, FMT_TORUS2D, FMT_DENSE = 0, 1, 2
 I8, I16, I32, FP8E4M3, BF16, F32, F64 = range(7)
-FLAG_ASYNC, FLAG_SKIP_VALIDATION, FLAG_STRICT_MONOTONE = 1, 2, 4
+FLAG_ASYNC, FLAG_SKIP_VALIDATION, FLAG_STRICT_MONOTONE, FLAG_SINGLE_STEP = 1, 2, 4, 8
 
 _vp = ctypes.c_void_p
 

@@ -787,10 +787,22 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
     if (!done && iters > 0) {
         DOCH_CHECK(c->ping.ensure(xbytes));
         void *cur = xd, *nxt = c->ping.ptr;
-        for (int k = 0; k < iters; ++k) {
+        const bool pairs_ok = !Hd && c->format == ISING_FMT_TORUS2D && xtype == ISING_F32 &&
+                              !(c->flags & ISING_FLAG_SINGLE_STEP) &&
+                              torus_pair_ok(c, static_cast<const float *>(cur), static_cast<const float *>(nxt), R);
+        for (int k = 0; k < iters;) {
+            if (pairs_ok && k + 1 < iters) {  // two steps in one pass over the lattice
+                const double a1 = alpha_h[alpha_len == 1 ? 0 : k], a2 = alpha_h[alpha_len == 1 ? 0 : k + 1];
+                DOCH_CHECK(torus_pair_f32(c, static_cast<const float *>(cur), static_cast<float *>(nxt),
+                                          static_cast<float>(a1), static_cast<float>(a2), 1.0 / beta_h[0], st));
+                std::swap(cur, nxt);
+                k += 2;
+                continue;
+            }
             if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
             DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
             std::swap(cur, nxt);
+            ++k;
         }
         if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, iters - 1, Hd + static_cast<size_t>(iters) * pairs, st));
         if (cur != xd) DOCH_CUDA(cudaMemcpyAsync(xd, cur, xbytes, cudaMemcpyDeviceToDevice, st));

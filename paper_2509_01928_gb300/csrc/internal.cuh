@@ -121,6 +121,11 @@ ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *
                               float alpha, double inv_beta, cudaStream_t st);
 ising_status_t torus_step_f64(const ising_context *c, const double *x_in, double *x_out, int R,
                               double alpha, double beta, cudaStream_t st);
+// TORUS2D, two DOCH steps in one pass (alpha1 then alpha2), FP32, R = 1; only
+// when torus_pair_ok() holds.
+bool torus_pair_ok(const ising_context *c, const float *x_in, const float *x_out, int R);
+ising_status_t torus_pair_f32(const ising_context *c, const float *x_in, float *x_out, float alpha1,
+                              float alpha2, double inv_beta, cudaStream_t st);
 
 // Per-instance parameter tables on the device (filled by ising_iterate):
 // alpha [n_inst][alpha_len] and beta [n_inst] in FP64, plus FP32 copies of

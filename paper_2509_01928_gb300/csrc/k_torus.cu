@@ -32,9 +32,64 @@ namespace {
 constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
-// sign-extended byte k (0..3) of a packed word of four int8
+// Signed byte k (0..3) of a packed word of four int8, as a float, without an
+// integer-to-float conversion: flipping the sign bit maps s to s + 128 in
+// 0..255, which is placed in the low mantissa byte of 2^23; subtracting
+// 2^23 + 128 leaves s exactly.
 __device__ __forceinline__ float sbyte(int v, int k) {
+    const unsigned b = static_cast<unsigned>(v) ^ 0x80808080u;
+    return __uint_as_float(__byte_perm(b, 0x4B000000u, 0x7540u | static_cast<unsigned>(k))) - 8388736.0f;
+}
+// The same value by shifts and a conversion: fewer live constants, which the
+// 40-register single-step kernel needs.
+__device__ __forceinline__ float sbyte_cvt(int v, int k) {
     return static_cast<float>((v << (24 - 8 * k)) >> 24);
+}
+
+// One site of Eq. FPE: u = sum over the four neighbours (right, left, down,
+// up -- always in this order), then cbrt((u + alpha x) / beta). Both stencil
+// kernels use these two functions, so a fused two-step pass reproduces two
+// single steps exactly.
+__device__ __forceinline__ float site_sum(float wr, float xr, float wl, float xl, float wd, float xd,
+                                          float wu, float xu) {
+    return wr * xr + wl * xl + wd * xd + wu * xu;
+}
+
+__device__ __forceinline__ float site_new(float u, float x, float alpha, float zscale, float xscale) {
+    return cbrt_pow2((u + alpha * x) * zscale) * xscale;
+}
+
+// four consecutive sites c..c+3 of one row: xm row values, xl/xr the values
+// left of c and right of c+3, xu/xd the rows above/below, rt the packed right
+// couplings of the row, wleft the coupling to column c-1, dd/du the down
+// couplings of this row / of the row above (as floats)
+__device__ __forceinline__ float4 row4_new_w(float4 xm, float xl, float xr, float4 xu, float4 xd,
+                                             const float (&wr)[4], float wleft, const float (&dd)[4],
+                                             const float (&du)[4], float alpha, float zscale, float xscale) {
+    const float w0 = wr[0], w1 = wr[1], w2 = wr[2], w3 = wr[3];
+    float4 out;
+    out.x = site_new(site_sum(w0, xm.y, wleft, xl, dd[0], xd.x, du[0], xu.x), xm.x, alpha, zscale, xscale);
+    out.y = site_new(site_sum(w1, xm.z, w0, xm.x, dd[1], xd.y, du[1], xu.y), xm.y, alpha, zscale, xscale);
+    out.z = site_new(site_sum(w2, xm.w, w1, xm.y, dd[2], xd.z, du[2], xu.z), xm.z, alpha, zscale, xscale);
+    out.w = site_new(site_sum(w3, xr, w2, xm.z, dd[3], xd.w, du[3], xu.w), xm.w, alpha, zscale, xscale);
+    return out;
+}
+
+__device__ __forceinline__ void unpack4(int v, float (&f)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[k] = sbyte(v, k);
+}
+__device__ __forceinline__ void unpack4_cvt(int v, float (&f)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[k] = sbyte_cvt(v, k);
+}
+
+__device__ __forceinline__ float4 row4_new(float4 xm, float xl, float xr, float4 xu, float4 xd, int rt,
+                                           float wleft, const float (&dd)[4], const float (&du)[4], float alpha,
+                                           float zscale, float xscale) {
+    float wr[4];
+    unpack4_cvt(rt, wr);
+    return row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha, zscale, xscale);
 }
 
 // 40 registers: 6 CTAs (1536 threads) per SM keep enough loads in flight
@@ -71,8 +126,8 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
     int64_t od = o + Lc == n ? 0 : o + Lc;             // row r+1
     float4 xu = ldx(ou), xm = ldx(o);
     float hm = ldh(o);
-    const int dup = ldw(dc, ou);
-    float du0 = sbyte(dup, 0), du1 = sbyte(dup, 1), du2 = sbyte(dup, 2), du3 = sbyte(dup, 3);
+    float du[4];
+    unpack4_cvt(ldw(dc, ou), du);
     float4 xd = ldx(od);
     float hd = ldh(od);
     int dm = ldw(dc, o), rt = ldw(rc, o);
@@ -94,28 +149,167 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
         float xl = __shfl_up_sync(kFull, xm.w, 1);
         float xr = __shfl_down_sync(kFull, xm.x, 1);
         const int rtl = __shfl_up_sync(kFull, rt, 1);
-        float wleft = sbyte(rtl, 3);
+        float wleft = sbyte_cvt(rtl, 3);
         if (is_l) { xl = hm; wleft = wl; }
         if (is_r) xr = hm;
 
-        const float w0 = sbyte(rt, 0), w1 = sbyte(rt, 1), w2 = sbyte(rt, 2), w3 = sbyte(rt, 3);
-        const float d0 = sbyte(dm, 0), d1 = sbyte(dm, 1), d2 = sbyte(dm, 2), d3 = sbyte(dm, 3);
-        const float u0 = w0 * xm.y + wleft * xl + d0 * xd.x + du0 * xu.x;
-        const float u1 = w1 * xm.z + w0 * xm.x + d1 * xd.y + du1 * xu.y;
-        const float u2 = w2 * xm.w + w1 * xm.y + d2 * xd.z + du2 * xu.z;
-        const float u3 = w3 * xr + w2 * xm.z + d3 * xd.w + du3 * xu.w;
-        float4 out;
-        out.x = cbrt_pow2((u0 + alpha * xm.x) * zscale) * xscale;
-        out.y = cbrt_pow2((u1 + alpha * xm.y) * zscale) * xscale;
-        out.z = cbrt_pow2((u2 + alpha * xm.z) * zscale) * xscale;
-        out.w = cbrt_pow2((u3 + alpha * xm.w) * zscale) * xscale;
+        float dd[4];
+        unpack4_cvt(dm, dd);
+        const float4 out = row4_new(xm, xl, xr, xu, xd, rt, wleft, dd, du, alpha, zscale, xscale);
         if (active) __stcs(reinterpret_cast<float4 *>(oc + o), out);
 
         xu = xm; xm = xd; hm = hd;
-        du0 = d0; du1 = d1; du2 = d2; du3 = d3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) du[q] = dd[q];
         xd = xn; hd = hn; dm = dn; rt = rn; wl = wn;
         o = on; od = onn;
     }
+}
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Output column groups per warp of the two-step kernel: lanes 1..30. Lanes 0
+// and 31 load the groups on either side and compute with the rest of the
+// warp; their intermediate values at their three inner columns are exact
+// (two steps need a halo of two columns, a lane holds four), their outer
+// columns are wrong and never used, and they write nothing.
+constexpr int kSeg = 30;
+
+// Per-thread shared-memory ring of the two-step kernel: D slots, each holding
+// one lattice row's loads of every thread (its float4 of x and its two packed
+// coupling words).
+template <int D>
+struct T2Ring {
+    float4 x[D][kThreads];
+    int rw[D][kThreads];
+    int dw[D][kThreads];
+};
+
+// Two DOCH steps per pass (temporal blocking): x^(k+2) from x^(k), with the
+// intermediate x^(k+1) held in registers. Every warp is an independent unit
+// owning kSeg column groups of 4 columns and a strip of rows [r0, r1); it
+// walks down the strip computing y = x^(k+1) for row r from x rows r-1..r+1,
+// then z = x^(k+2) for row r-1 from y rows r-2..r, reading x rows
+// r0-2 .. r1+1. Loads are staged D rows ahead by cp.async into a per-thread
+// ring in shared memory (no registers held by the prefetch); each thread reads
+// only the slots it filled, so cp.async.wait_group is the only
+// synchronisation. HBM traffic per site and step is about half that of the
+// single-step kernel (the halo lanes add 2/30 to the reads); every site is
+// computed by the same helpers, so the pass equals two single steps bit for
+// bit.
+template <int D>
+__global__ void __launch_bounds__(kThreads, 3)
+torus_f32_r1_vec4_t2(const float *__restrict__ xi, float *__restrict__ xo,
+                     const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
+                     int segs, int bpt, float alpha1, float alpha2, float zscale, float xscale) {
+    extern __shared__ __align__(16) unsigned char t2_smem[];
+    T2Ring<D> &ring = *reinterpret_cast<T2Ring<D> *>(t2_smem);
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = blockIdx.x * (kThreads / 32) + (t >> 5);
+    const int seg = warp % segs;
+    const int part = warp / segs;
+    if (part >= bpt) return;  // uniform over the warp; nothing below synchronises the block
+    const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
+    const int r1 = static_cast<int>(static_cast<int64_t>(Lr) * (part + 1) / bpt);
+    if (r0 >= r1) return;  // uniform over the warp
+
+    // column group of this lane, wrapped periodically so that consecutive
+    // lanes always hold consecutive groups of the torus
+    const int ncol4 = Lc >> 2;
+    const int g = seg * kSeg + lane - 1;
+    const bool writes = lane >= 1 && lane <= kSeg && g < ncol4;
+    const int c = (((g % ncol4) + ncol4) % ncol4) * 4;
+    const int64_t n = static_cast<int64_t>(Lr) * Lc;
+    const float *xc = xi + c;
+    const int8_t *rc = right + c, *dc = down + c;
+    auto wrap_up = [&](int64_t o) { return o == 0 ? n - Lc : o - Lc; };
+    auto wrap_dn = [&](int64_t o) { o += Lc; return o == n ? int64_t(0) : o; };
+    auto issue = [&](unsigned s, int64_t o) {
+        cp_async16(&ring.x[s][t], xc + o);
+        cp_async4(&ring.rw[s][t], rc + o);
+        cp_async4(&ring.dw[s][t], dc + o);
+    };
+
+    // rows r0-2 and r0-1 are read directly; the ring then carries rows r0 .. r1+1
+    const int64_t o0 = static_cast<int64_t>(r0) * Lc;
+    const int64_t om = wrap_up(o0), omm = wrap_up(om);
+    float4 xu = __ldg(reinterpret_cast<const float4 *>(xc + omm));
+    float4 xm = __ldg(reinterpret_cast<const float4 *>(xc + om));
+    float du[4];
+    unpack4(__ldg(reinterpret_cast<const int *>(dc + omm)), du);
+    int dm = __ldg(reinterpret_cast<const int *>(dc + om));
+    int rt = __ldg(reinterpret_cast<const int *>(rc + om));
+    const int rows = r1 - r0 + 2;  // ring bundles: rows r0 .. r1+1
+    int64_t oi = o0;                // offset of the next row to stage
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        if (q < rows) {
+            issue(q, oi);
+            oi = wrap_dn(oi);
+        }
+        cp_async_commit();
+    }
+    int64_t os = o0;  // offset of the next output row of step 2 (rows r0, r0+1, ...)
+    float4 ya = make_float4(0.f, 0.f, 0.f, 0.f), yb = ya;
+    float wr_p[4] = {0.f, 0.f, 0.f, 0.f};
+    float du_p[4] = {0.f, 0.f, 0.f, 0.f};
+
+    // iteration i handles step-1 row r = r0-1+i and step-2 row r-1; unrolled
+    // by 3 so the two-row histories (x, y, down couplings) rotate by renaming
+#pragma unroll 3
+    for (int i = 0; i < rows; ++i) {
+        // the bundle of row r+1 (ring index i) has landed: older groups complete first
+        cp_async_wait<D - 1>();
+        const unsigned s = static_cast<unsigned>(i) % D;
+        const float4 xd = ring.x[s][t];
+        const int rt_n = ring.rw[s][t], dm_n = ring.dw[s][t];
+        // every read of slot s is above; refill it with ring index i+D
+        if (i + D < rows) {
+            issue(s, oi);
+            oi = wrap_dn(oi);
+        }
+        cp_async_commit();
+
+        // ---- step 1: y row r
+        float wr[4], dd[4];
+        unpack4(rt, wr);
+        unpack4(dm, dd);
+        const float xl = __shfl_up_sync(kFull, xm.w, 1);
+        const float xr = __shfl_down_sync(kFull, xm.x, 1);
+        const float wleft = __shfl_up_sync(kFull, wr[3], 1);
+        const float4 yc = row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha1, zscale, xscale);
+
+        // ---- step 2: z row r-1 from y rows r-2, r-1, r (once y row r0-1 is two rows back)
+        if (i > 1) {
+            const float yl = __shfl_up_sync(kFull, yb.w, 1);
+            const float yr = __shfl_down_sync(kFull, yb.x, 1);
+            const float wleftp = __shfl_up_sync(kFull, wr_p[3], 1);
+            const float4 z = row4_new_w(yb, yl, yr, ya, yc, wr_p, wleftp, du, du_p, alpha2, zscale, xscale);
+            if (writes) __stcs(reinterpret_cast<float4 *>(xo + c + os), z);
+            os = wrap_dn(os);
+        }
+
+        // ---- rotate
+        ya = yb; yb = yc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { wr_p[q] = wr[q]; du_p[q] = du[q]; du[q] = dd[q]; }
+        xu = xm; xm = xd;
+        dm = dm_n; rt = rt_n;
+    }
+    cp_async_wait<0>();
 }
 
 // Any R, float or double, any alignment: one thread per (site, replica).
@@ -143,6 +337,23 @@ __global__ void torus_generic(const T *__restrict__ xi, T *__restrict__ xo,
         else
             xo[t] = cbrt(z / beta);
     }
+}
+
+// ring depth of the two-step kernel: rows staged ahead of the one in use
+constexpr int kT2Depth = 4;
+constexpr size_t kT2Smem = sizeof(T2Ring<kT2Depth>);
+
+int t2_blocks_per_sm() {
+    static int occ = 0;
+    if (!occ) {
+        if (cudaFuncSetAttribute(torus_f32_r1_vec4_t2<kT2Depth>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kT2Smem)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, torus_f32_r1_vec4_t2<kT2Depth>, kThreads,
+                                                          kT2Smem) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+    }
+    return occ;
 }
 
 int vec4_blocks_per_sm() {
@@ -184,6 +395,36 @@ ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *
         torus_generic<float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
             x_in, x_out, c->right, c->down, Lr, Lc, R, alpha, static_cast<float>(inv_beta));
     }
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+bool torus_pair_ok(const ising_context *c, const float *x_in, const float *x_out, int R) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(x_in) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(x_out) % 16 == 0);
+    return R == 1 && c->l_cols % 4 == 0 && aligned && c->l_rows >= 4 && c->l_rows < (1LL << 31) &&
+           c->l_cols < (1LL << 31);
+}
+
+ising_status_t torus_pair_f32(const ising_context *c, const float *x_in, float *x_out, float alpha1,
+                              float alpha2, double inv_beta, cudaStream_t st) {
+    const int64_t Lr = c->l_rows, Lc = c->l_cols;
+    const int64_t ncol4 = Lc / 4;
+    const int64_t segs = (ncol4 + kSeg - 1) / kSeg;
+    // one warp per (column segment, row strip); fill every warp slot of the GPU once
+    const int64_t warp_slots = static_cast<int64_t>(c->num_sms) * t2_blocks_per_sm() * (kThreads / 32);
+    int64_t bpt = warp_slots / segs;
+    if (bpt < 1) bpt = 1;
+    if (bpt > Lr / 4) bpt = Lr / 4 > 0 ? Lr / 4 : 1;
+    const int64_t warps = segs * bpt;
+    const int64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > INT32_MAX || segs > INT32_MAX) return fail(ISING_ERR_UNSUPPORTED, "lattice too large");
+    const int k = cbrt_prescale_exp(inv_beta);
+    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+    const float xscale = std::ldexp(1.0f, -k);
+    torus_f32_r1_vec4_t2<kT2Depth><<<static_cast<unsigned>(blocks), kThreads, kT2Smem, st>>>(
+        x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), static_cast<int>(segs),
+        static_cast<int>(bpt), alpha1, alpha2, zscale, xscale);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

@@ -124,6 +124,25 @@ def test_torus_generic(shape, R, dtype):
         _close(x.cpu().numpy(), ref, TOL32 if dtype == np.float32 else TOL64)
 
 
+@pytest.mark.parametrize("shape", [(37, 1028), (16, 2048), (9, 4), (5, 8), (64, 1024), (100, 3000),
+                                   (4, 120), (7, 124), (300, 968)])
+@pytest.mark.parametrize("iters", [2, 3, 8, 41])
+def test_torus_fused_pairs_match_single_steps(shape, iters):
+    """The two-step pass computes every site with the single-step arithmetic:
+    bit-identical iterates, including an odd remainder step and an alpha schedule."""
+    t = I.torus_pm1(*shape, seed=107)
+    x0 = I.x0_uniform(t.n, 1, seed=108)
+    alpha, beta = O.alpha_beta(t, eta=1.0, method="wigner")
+    sched = alpha * (1.0 + 0.05 * np.sin(np.arange(iters)))
+    out = []
+    for flags in (0, N.FLAG_SINGLE_STEP):
+        with Handle(t, flags=flags) as h:
+            x = _dev(x0)
+            N.ising_iterate(h, x, sched, [beta], iters)
+            out.append(x.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_torus_host_buffers_match_device():
     t = I.torus_pm1(20, 64, seed=105)
     x0 = I.x0_uniform(t.n, 1, seed=106)
