@@ -443,19 +443,25 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
         DOCH_CHECK(upload(&c->right, hp.right.data(), hp.right.size()));
         DOCH_CHECK(upload(&c->down, hp.down.data(), hp.down.size()));
     } else {
-        // BF16 copy with the leading dimension rounded up to 8 (16-byte rows for TMA)
-        const int64_t n = hp.n, ld = (n + 7) / 8 * 8;
-        std::vector<uint16_t> bf(static_cast<size_t>(n) * ld, 0);
+        // BF16 copy in the tensor-core tile order: [row tile of 128][K block of 64][128][64],
+        // each 16 KB block 128-byte swizzled (chunk c of row r at c ^ (r & 7)), zero padded
+        const int64_t n = hp.n, ld = (n + 63) / 64 * 64, mt = (n + 127) / 128, kbs = ld / 64;
+        std::vector<uint16_t> bf(static_cast<size_t>(mt) * 128 * ld, 0);
         long long jsum = 0;
-        for (int64_t i = 0; i < n; ++i)
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t ti = i / 128, ri = i % 128;
             for (int64_t j = 0; j < n; ++j) {
                 const double v = value_at(hp.dense.data(), hp.jtype, i * n + j);
                 float f = static_cast<float>(v);
                 uint32_t u;
                 std::memcpy(&u, &f, 4);
-                bf[static_cast<size_t>(i) * ld + j] = static_cast<uint16_t>(u >> 16);  // exact: |v| <= 256 integer
+                const int64_t kb = j / 64, cc = j % 64;
+                const size_t off = static_cast<size_t>(((ti * kbs + kb) * 128 + ri) * 64 +
+                                                       ((((cc >> 3) ^ ri) & 7) << 3) + (cc & 7));
+                bf[off] = static_cast<uint16_t>(u >> 16);  // exact: |v| <= 256 integer
                 jsum += static_cast<long long>(v);
             }
+        }
         DOCH_CHECK(upload(&c->dense, bf.data(), bf.size() * 2));
         c->dense_type = ISING_BF16;
         c->dense_ld = ld;

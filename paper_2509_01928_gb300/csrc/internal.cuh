@@ -80,8 +80,9 @@ struct ising_context {
     // TORUS2D
     int64_t l_rows = 0, l_cols = 0;
     int8_t *right = nullptr, *down = nullptr;
-    // DENSE: integer couplings held as BF16 [n][dense_ld] (exact for |J| <= 256),
-    // dense_ld = n rounded up to 8 (zero padded) for 16-byte TMA strides
+    // DENSE: integer couplings held as BF16 (exact for |J| <= 256) in the
+    // tensor-core tile order [ceil(n/128)][dense_ld/64][128][64], 128-byte
+    // swizzled; dense_ld = n rounded up to 64 (zero padded)
     void *dense = nullptr;
     int dense_type = 0;
     int64_t dense_ld = 0;

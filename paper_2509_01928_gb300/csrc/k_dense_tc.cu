@@ -8,24 +8,34 @@
 // is exact in BF16 and every (J S) entry is an integer below 2^24, so the FP32
 // accumulator and the int64 reduction are exact.
 //
-// Layout: J is BF16 [n_pad rows][ld] row-major (ld = n rounded up to 8,
-// zero padded); the iterate is held replica-major, Xt [R_pad][ld] BF16, so
-// both MMA operands are K-major. Tiles: one CTA per (128 rows of J) x
-// (N = up to 256 replicas).
+// Layout: both operands are stored in HBM as the exact shared-memory images
+// the MMA reads, so every pipeline stage is two contiguous bulk copies
+// (DRAM pages are read whole, no tensor maps):
+//   J  : [m_tiles][kblocks][128 rows][64 columns] BF16, each 16 KB block
+//        128-byte swizzled (16-byte chunk c of row r stored at chunk
+//        c ^ (r & 7)); rows >= n and columns >= n are zero.
+//   X  : replica-major [kblocks][R_pad][64] BF16 with the same swizzle, so
+//        the rows r0 .. r0+N-1 of one K block are one contiguous N x 128 B
+//        image; spins >= n are zero.
+// Tiles: one CTA per (128 rows of J) x (N = up to 256 replicas).
 //
 // Pipeline per CTA (256 threads):
-//   warp 0, one lane: TMA producer. K-block kb (64 columns of J = 64 rows of
-//     X) goes to stage kb % kStages: A tile 128 x 64 (16 KB), B tile N x 64,
-//     both 128-byte swizzled; arrival tracked by the stage's "full" mbarrier.
+//   warp 0, one lane: producer. K-block kb (64 columns of J = 64 spins of
+//     X) goes to stage kb % kStages by two cp.async.bulk copies: A tile
+//     128 x 64 (16 KB), B tile N x 64 (N x 128 B); arrival tracked by the
+//     stage's "full" mbarrier (complete_tx).
 //   warp 1, one lane: MMA issuer. Waits "full", issues four
 //     tcgen05.mma.kind::f16 (K = 16 each) into the TMEM accumulator, and
 //     tcgen05.commit's the stage's "empty" mbarrier (the producer may reuse
 //     it once the MMAs that read it complete). After the last block it
 //     commits the "accumulator ready" mbarrier.
 //   warp 2: allocates and frees the TMEM columns.
-//   warps 4-7: epilogue. Warp 4+q owns TMEM lanes (rows) 32q..32q+31; it
-//     reads the accumulator 32 columns at a time (tcgen05.ld 32x32b.x32) and
-//     writes the new iterate (or the energy partials).
+//   epilogue, all eight warps once the accumulator is ready: warp w owns
+//     TMEM lanes (rows) 32 (w % 4) .. +31 and every other 32-column block
+//     from block w / 4; it reads 32 columns at a time (tcgen05.ld 32x32b.x32)
+//     and writes the new iterate (cube root as sign(z) 2^(log2|z|/3) with the
+//     hardware lg2/ex2 on a power-of-two prescaled z; BF16 output) or the
+//     energy partials.
 // Every mbarrier wait is bounded (~1 s of %globaltimer); on expiry the CTA
 // sets the error word, drains its TMA copies (bounded), frees TMEM, returns.
 #include <cuda.h>
@@ -34,6 +44,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "cbrt.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -102,13 +113,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(saddr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
-        : "memory");
+// contiguous global -> shared copy (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+// element offset of (replica r, spin i) in the swizzled replica-major layout
+__host__ __device__ __forceinline__ size_t xs_index(int r, int i, int R_pad) {
+    const int kb = i >> 6, c = i & 63;
+    return (static_cast<size_t>(kb) * R_pad + r) * 64 + ((((c >> 3) ^ r) & 7) << 3) + (c & 7);
 }
 
 // K-major, 128-byte swizzled operand tile: rows are 128 bytes apart, groups of
@@ -164,18 +180,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // MODE 0: DOCH step into Xt_out. MODE 1: energy partials q_r into q_out (int64).
 template <int MODE>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constant__ CUtensorMap tmap_x,
-                const __nv_bfloat16 *__restrict__ xt_in, __nv_bfloat16 *__restrict__ xt_out,
-                const float *__restrict__ h, int n, int ld, int R, int n_tile, uint32_t tmem_cols,
-                float alpha, float inv_beta, long long *__restrict__ q_out, int *__restrict__ err) {
+dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__restrict__ xt_in,
+                __nv_bfloat16 *__restrict__ xt_out, const float *__restrict__ h, int n, int kblocks, int R,
+                int R_pad, int n_tile, uint32_t tmem_cols, float alpha, float zscale, float xscale,
+                long long *__restrict__ q_out, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
     const int r0 = blockIdx.y * n_tile;
-    const int kblocks = (ld + kBK - 1) / kBK;
+    constexpr uint32_t a_bytes = kBM * kBK * 2;
     const uint32_t b_bytes = static_cast<uint32_t>(n_tile) * kBK * 2;
+    const __nv_bfloat16 *a_src = jt + static_cast<size_t>(blockIdx.x) * kblocks * (kBM * kBK);
+    const __nv_bfloat16 *b_src = xt_in + static_cast<size_t>(r0) * kBK;
     volatile int *abort_flag = &sm.abort_flag;
 
     if (threadIdx.x == 0) {
@@ -199,27 +217,34 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constan
     const uint32_t tmem = sm.tmem_base;
 
     int issued = 0;  // producer: K-blocks whose copies were issued
+    // Each CTA walks K from its own starting block kb0 and wraps around, so at
+    // any moment the CTAs stream different parts of J (equal 4 MB-aligned
+    // offsets in lockstep would queue on the same DRAM channels) and read
+    // different blocks of X from L2. Sum order only changes FP32 rounding.
+    const int kb0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * kblocks / gridDim.x);
     if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) - 1) & 1, err, abort_flag)) break;
-            mbar_expect_tx(&sm.full[s], kBM * kBK * 2 + b_bytes);
-            tma_load_2d(sm.a[s], &tmap_j, kb * kBK, m0, &sm.full[s]);
-            tma_load_2d(sm.b[s], &tmap_x, kb * kBK, r0, &sm.full[s]);
-            issued = kb + 1;
+        for (int it = 0; it < kblocks; ++it) {
+            const int s = it % kStages;
+            int kb = kb0 + it;
+            if (kb >= kblocks) kb -= kblocks;
+            if (it >= kStages && !mbar_wait(&sm.empty[s], ((it / kStages) - 1) & 1, err, abort_flag)) break;
+            mbar_expect_tx(&sm.full[s], a_bytes + b_bytes);
+            bulk_load(sm.a[s], a_src + static_cast<size_t>(kb) * (kBM * kBK), a_bytes, &sm.full[s]);
+            bulk_load(sm.b[s], b_src + static_cast<size_t>(kb) * R_pad * kBK, b_bytes, &sm.full[s]);
+            issued = it + 1;
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = idesc_bf16(kBM, n_tile);
         bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (!mbar_wait(&sm.full[s], (kb / kStages) & 1, err, abort_flag)) { ok = false; break; }
+        for (int it = 0; it < kblocks; ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(&sm.full[s], (it / kStages) & 1, err, abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t ad = smem_desc_sw128(sm.a[s]);
             const uint64_t bd = smem_desc_sw128(sm.b[s]);
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k)  // K = 16 per MMA: +32 bytes = +2 in the descriptor
-                mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (it | k) != 0);
             mma_commit(&sm.empty[s]);
         }
         // the accumulator barrier also tracks completion of every MMA issued so far
@@ -229,31 +254,43 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constan
             while (!mbar_test(&sm.acc_ready, 0) && gtime() - t0 < kWaitNs) {
             }
         }
-    } else if (warp >= 4) {
-        const int q = warp - 4;
+    }
+    __syncwarp();
+    // Epilogue, all eight warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its
+    // 32 rows) and every other 32-column block starting at block w / 4.
+    {
+        const int q = warp & 3, half = warp >> 2;
         const int row = m0 + 32 * q + lane;
         // warp-uniform decision: tcgen05.ld below is a .sync.aligned warp instruction
         const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.acc_ready, 0, err, abort_flag) && !*abort_flag);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float hv = (h && row < n) ? h[row] : 0.f;
-            for (int c0 = 0; c0 < n_tile; c0 += 32) {
+            for (int c0 = 32 * half; c0 < n_tile; c0 += 64) {
                 float acc[32];
                 tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + c0, acc);
+                if (MODE == 0) {
+                    float xo[32];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const int r = r0 + c0 + k;
-                    if (MODE == 0) {
+                    for (int k = 0; k < 32; ++k) {  // all loads first
+                        const int r = r0 + c0 + k;
+                        xo[k] = (row < n && r < R) ? __bfloat162float(xt_in[xs_index(r, row, R_pad)]) : 0.f;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const int r = r0 + c0 + k;
                         if (row < n && r < R) {
-                            const size_t idx = static_cast<size_t>(r) * ld + row;
-                            const float xo = __bfloat162float(xt_in[idx]);
-                            const float z = (acc[k] + alpha * xo + hv) * inv_beta;
-                            xt_out[idx] = __float2bfloat16_rn(cbrtf(z));
+                            const float z = (acc[k] + alpha * xo[k] + hv) * zscale;
+                            xt_out[xs_index(r, row, R_pad)] = __float2bfloat16_rn(cbrt_pow2(z) * xscale);
                         }
-                    } else {
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const int r = r0 + c0 + k;
                         long long contrib = 0;
                         if (row < n && r < R) {
-                            const float s = __bfloat162float(xt_in[static_cast<size_t>(r) * ld + row]);
+                            const float s = __bfloat162float(xt_in[xs_index(r, row, R_pad)]);
                             contrib = static_cast<long long>(s) * static_cast<long long>(acc[k]);
                         }
 #pragma unroll
@@ -267,9 +304,9 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constan
     }
     // drain: the producer waits (bounded) until every copy it issued has landed
     if (warp == 0 && lane == 0 && *abort_flag) {
-        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb) {
+        for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
             const uint64_t t0 = gtime();
-            while (!mbar_test(&sm.full[kb % kStages], (kb / kStages) & 1) && gtime() - t0 < kWaitNs) {
+            while (!mbar_test(&sm.full[it % kStages], (it / kStages) & 1) && gtime() - t0 < kWaitNs) {
             }
         }
     }
@@ -281,9 +318,9 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap tmap_j, const __grid_constan
     }
 }
 
-// x [n][R] (caller layout, BF16) <-> Xt [R_pad][ld] (replica-major, zero padded)
+// x [n][R] (caller layout, BF16) <-> the swizzled replica-major layout
 __global__ void to_replica_major(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, int n,
-                                 int R, int ld) {
+                                 int R, int R_pad) {
     __shared__ __nv_bfloat16 tile[32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -293,17 +330,17 @@ __global__ void to_replica_major(const __nv_bfloat16 *__restrict__ x, __nv_bfloa
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int r = r0 + k, i = i0 + threadIdx.x;
-        if (r < R && i < n) xt[static_cast<size_t>(r) * ld + i] = tile[threadIdx.x][k];
+        if (r < R && i < n) xt[xs_index(r, i, R_pad)] = tile[threadIdx.x][k];
     }
 }
 
 __global__ void from_replica_major(const __nv_bfloat16 *__restrict__ xt, __nv_bfloat16 *__restrict__ x, int n,
-                                   int R, int ld) {
+                                   int R, int R_pad) {
     __shared__ __nv_bfloat16 tile[32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int r = r0 + k, i = i0 + threadIdx.x;
-        tile[k][threadIdx.x] = (r < R && i < n) ? xt[static_cast<size_t>(r) * ld + i] : __float2bfloat16_rn(0.f);
+        tile[k][threadIdx.x] = (r < R && i < n) ? xt[xs_index(r, i, R_pad)] : __float2bfloat16_rn(0.f);
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -315,7 +352,7 @@ __global__ void from_replica_major(const __nv_bfloat16 *__restrict__ xt, __nv_bf
 // spins (BF16 +1/-1, sign(0) = +1) of iterates of any supported type, replica-major
 template <typename XT>
 __global__ void spins_replica_major(const XT *__restrict__ x, __nv_bfloat16 *__restrict__ st, int n, int R,
-                                    int ld) {
+                                    int R_pad) {
     const int64_t total = static_cast<int64_t>(n) * R;
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -324,16 +361,16 @@ __global__ void spins_replica_major(const XT *__restrict__ x, __nv_bfloat16 *__r
         float v;
         if constexpr (sizeof(XT) == 2) v = __bfloat162float(x[t]);
         else v = static_cast<float>(x[t]);
-        st[static_cast<size_t>(r) * ld + i] = __float2bfloat16_rn(v >= 0.f ? 1.f : -1.f);
+        st[xs_index(r, static_cast<int>(i), R_pad)] = __float2bfloat16_rn(v >= 0.f ? 1.f : -1.f);
     }
 }
 
 __global__ void field_dot_spins(const __nv_bfloat16 *__restrict__ st, const int64_t *__restrict__ h, int n,
-                                int ld, long long *__restrict__ hs) {
+                                int R_pad, long long *__restrict__ hs) {
     const int r = blockIdx.y;
     long long acc = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        acc += h[i] * static_cast<long long>(__bfloat162float(st[static_cast<size_t>(r) * ld + i]));
+        acc += h[i] * static_cast<long long>(__bfloat162float(st[xs_index(r, i, R_pad)]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(hs + r),
@@ -353,48 +390,15 @@ __global__ void dense_energy_finish(const long long *__restrict__ q, const long 
     if (cut_d) cut_d[r] = static_cast<double>(cut);
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-ising_status_t encode_fn(EncodeTiled *out) {
-    static EncodeTiled fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        DOCH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        if (!p || q != cudaDriverEntryPointSuccess)
-            return fail(ISING_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    *out = fn;
-    return ISING_OK;
-}
-
-// 2-D BF16 map over [rows][ld], box = 64 columns x box_rows rows, 128-byte swizzle
-ising_status_t make_map(CUtensorMap *map, const void *base, int ld, int rows, int box_rows) {
-    EncodeTiled enc;
-    DOCH_CHECK(encode_fn(&enc));
-    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows)};
-    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(ISING_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
-    return ISING_OK;
-}
-
 struct DenseGeom {
-    int n, ld, R, R_pad, n_tile, m_tiles, r_tiles;
+    int n, kblocks, R, R_pad, n_tile, m_tiles, r_tiles;
     uint32_t tmem_cols;
 };
 
 DenseGeom geometry(const ising_context *c, int R) {
     DenseGeom g;
     g.n = static_cast<int>(c->n);
-    g.ld = static_cast<int>(c->dense_ld);
+    g.kblocks = static_cast<int>(c->dense_ld / kBK);
     g.R = R;
     g.R_pad = R <= 256 ? ((R + 15) / 16) * 16 : ((R + 255) / 256) * 256;
     g.n_tile = g.R_pad < 256 ? g.R_pad : 256;
@@ -409,14 +413,15 @@ DenseGeom geometry(const ising_context *c, int R) {
 size_t smem_bytes() { return sizeof(DenseSmem) + 1024; }
 
 template <int MODE>
-ising_status_t launch_dense(const DenseGeom &g, const CUtensorMap &mj, const CUtensorMap &mx,
-                            const __nv_bfloat16 *xt_in, __nv_bfloat16 *xt_out, const float *h, float alpha,
-                            float inv_beta, long long *q_out, int *err, cudaStream_t st) {
+ising_status_t launch_dense(const ising_context *c, const DenseGeom &g, const __nv_bfloat16 *xt_in,
+                            __nv_bfloat16 *xt_out, const float *h, float alpha, float zscale, float xscale,
+                            long long *q_out, cudaStream_t st) {
     auto kern = dense_tc_kernel<MODE>;
     DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes())));
     dim3 grid(static_cast<unsigned>(g.m_tiles), static_cast<unsigned>(g.r_tiles));
-    kern<<<grid, kThreadsTC, smem_bytes(), st>>>(mj, mx, xt_in, xt_out, h, g.n, g.ld, g.R, g.n_tile, g.tmem_cols,
-                                                 alpha, inv_beta, q_out, err);
+    kern<<<grid, kThreadsTC, smem_bytes(), st>>>(static_cast<const __nv_bfloat16 *>(c->dense), xt_in, xt_out, h, g.n,
+                                                 g.kblocks, g.R, g.R_pad, g.n_tile, g.tmem_cols, alpha, zscale,
+                                                 xscale, q_out, c->err_word);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
@@ -426,27 +431,26 @@ ising_status_t launch_dense(const DenseGeom &g, const CUtensorMap &mj, const CUt
 ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alpha_h, int alpha_len,
                              double beta, int iters, cudaStream_t st) {
     const DenseGeom g = geometry(c, R);
-    const size_t xt_bytes = static_cast<size_t>(g.R_pad) * g.ld * 2;
+    const size_t xt_bytes = static_cast<size_t>(g.R_pad) * g.kblocks * kBK * 2;
     DOCH_CHECK(c->work.ensure(2 * xt_bytes));
     __nv_bfloat16 *xt[2] = {c->work.as<__nv_bfloat16>(),
                             reinterpret_cast<__nv_bfloat16 *>(c->work.as<unsigned char>() + xt_bytes)};
     DOCH_CUDA(cudaMemsetAsync(c->work.ptr, 0, 2 * xt_bytes, st));
     dim3 tb(32, 8), tg((g.n + 31) / 32, (R + 31) / 32);
-    to_replica_major<<<tg, tb, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), xt[0], g.n, R, g.ld);
+    to_replica_major<<<tg, tb, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), xt[0], g.n, R, g.R_pad);
     DOCH_CUDA(cudaGetLastError());
-    CUtensorMap mj, mx[2];
-    DOCH_CHECK(make_map(&mj, c->dense, g.ld, g.n, kBM));
-    DOCH_CHECK(make_map(&mx[0], xt[0], g.ld, g.R_pad, g.n_tile));
-    DOCH_CHECK(make_map(&mx[1], xt[1], g.ld, g.R_pad, g.n_tile));
-    const float inv_beta = static_cast<float>(1.0 / beta);
+    // cube root on (z 2^(3k)) / beta, rescaled by 2^-k (exact powers of two, k from beta)
+    const double inv_beta = 1.0 / beta;
+    const int ks = cbrt_prescale_exp(inv_beta);
+    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * ks));
+    const float xscale = std::ldexp(1.0f, -ks);
     int cur = 0;
     for (int k = 0; k < iters; ++k) {
         const float a = static_cast<float>(alpha_h[alpha_len == 1 ? 0 : k]);
-        DOCH_CHECK(launch_dense<0>(g, mj, mx[cur], xt[cur], xt[1 - cur], c->h_f32, a, inv_beta, nullptr,
-                                   c->err_word, st));
+        DOCH_CHECK(launch_dense<0>(c, g, xt[cur], xt[1 - cur], c->h_f32, a, zscale, xscale, nullptr, st));
         cur = 1 - cur;
     }
-    from_replica_major<<<tg, tb, 0, st>>>(xt[cur], static_cast<__nv_bfloat16 *>(x), g.n, R, g.ld);
+    from_replica_major<<<tg, tb, 0, st>>>(xt[cur], static_cast<__nv_bfloat16 *>(x), g.n, R, g.R_pad);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
@@ -454,7 +458,7 @@ ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alp
 ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
                             double *E_d, double *cut_d, cudaStream_t st) {
     const DenseGeom g = geometry(c, R);
-    const size_t st_bytes = static_cast<size_t>(g.R_pad) * g.ld * 2;
+    const size_t st_bytes = static_cast<size_t>(g.R_pad) * g.kblocks * kBK * 2;
     DOCH_CHECK(c->partials.ensure(st_bytes + 2 * sizeof(long long) * R + 256));
     __nv_bfloat16 *sp = c->partials.as<__nv_bfloat16>();
     long long *q = reinterpret_cast<long long *>(c->partials.as<unsigned char>() + ((st_bytes + 255) & ~size_t(255)));
@@ -464,20 +468,17 @@ ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, i
     int64_t blocks = (total + 255) / 256;
     if (blocks > 16LL * c->num_sms) blocks = 16LL * c->num_sms;
     switch (xtype) {
-        case ISING_BF16: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), sp, g.n, R, g.ld); break;
-        case ISING_F32: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const float *>(x), sp, g.n, R, g.ld); break;
-        case ISING_F64: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const double *>(x), sp, g.n, R, g.ld); break;
-        case ISING_I8: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const int8_t *>(x), sp, g.n, R, g.ld); break;
+        case ISING_BF16: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), sp, g.n, R, g.R_pad); break;
+        case ISING_F32: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const float *>(x), sp, g.n, R, g.R_pad); break;
+        case ISING_F64: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const double *>(x), sp, g.n, R, g.R_pad); break;
+        case ISING_I8: spins_replica_major<<<blocks, 256, 0, st>>>(static_cast<const int8_t *>(x), sp, g.n, R, g.R_pad); break;
         default: return fail(ISING_ERR_INVALID_ARG, "dense energy: x type");
     }
     DOCH_CUDA(cudaGetLastError());
-    CUtensorMap mj, ms;
-    DOCH_CHECK(make_map(&mj, c->dense, g.ld, g.n, kBM));
-    DOCH_CHECK(make_map(&ms, sp, g.ld, g.R_pad, g.n_tile));
-    DOCH_CHECK(launch_dense<1>(g, mj, ms, sp, nullptr, nullptr, 0.f, 0.f, q, c->err_word, st));
+    DOCH_CHECK(launch_dense<1>(c, g, sp, nullptr, nullptr, 0.f, 0.f, 0.f, q, st));
     if (c->h_i64) {
         dim3 fg(static_cast<unsigned>((g.n + 255) / 256 < 64 ? (g.n + 255) / 256 : 64), static_cast<unsigned>(R));
-        field_dot_spins<<<fg, 256, 0, st>>>(sp, c->h_i64, g.n, g.ld, hs);
+        field_dot_spins<<<fg, 256, 0, st>>>(sp, c->h_i64, g.n, g.R_pad, hs);
         DOCH_CUDA(cudaGetLastError());
     }
     dense_energy_finish<<<(R + 127) / 128, 128, 0, st>>>(q, hs, c->dense_jsum, R, E_i, cut_i, E_d, cut_d);
