@@ -443,12 +443,37 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
         DOCH_CHECK(upload(&c->right, hp.right.data(), hp.right.size()));
         DOCH_CHECK(upload(&c->down, hp.down.data(), hp.down.size()));
     } else {
-        // BF16 copy in the tensor-core tile order: [row tile of 128][K block of 64][128][64],
-        // each 16 KB block 128-byte swizzled (chunk c of row r at c ^ (r & 7)), zero padded
+        // Tensor-core tile order [row tile of 128][K block of 64][128][64], zero padded. Entries
+        // all in {-1, 0, +1}: packed 2-bit codes (2 KB per tile, expanded on chip); otherwise a
+        // BF16 copy, each 16 KB block 128-byte swizzled (chunk c of row r at c ^ (r & 7)).
         const int64_t n = hp.n, ld = (n + 63) / 64 * 64, mt = (n + 127) / 128, kbs = ld / 64;
-        std::vector<uint16_t> bf(static_cast<size_t>(mt) * 128 * ld, 0);
+        bool ternary = true;
+        for (int64_t e = 0; e < n * n && ternary; ++e) {
+            const double v = value_at(hp.dense.data(), hp.jtype, e);
+            ternary = v == 0.0 || v == 1.0 || v == -1.0;
+        }
         long long jsum = 0;
-        for (int64_t i = 0; i < n; ++i) {
+        if (ternary) {
+            std::vector<uint8_t> packed(static_cast<size_t>(mt) * kbs * 2048, 0);
+            for (int64_t i = 0; i < n; ++i) {
+                const int64_t ti = i / 128, ri = i % 128;
+                for (int64_t j = 0; j < n; ++j) {
+                    const double v = value_at(hp.dense.data(), hp.jtype, i * n + j);
+                    const int64_t kb = j / 64, cc = j % 64;
+                    const uint8_t code = v > 0 ? 1 : (v < 0 ? 2 : 0);
+                    packed[static_cast<size_t>((ti * kbs + kb) * 2048 + ri * 16 + cc / 4)] |=
+                        static_cast<uint8_t>(code << (2 * (cc % 4)));
+                    jsum += static_cast<long long>(v);
+                }
+            }
+            DOCH_CHECK(upload(&c->dense, packed.data(), packed.size()));
+            c->dense_ternary = true;
+            c->dense_type = ISING_I8;
+            c->dense_ld = ld;
+            c->dense_jsum = jsum;
+        }
+        std::vector<uint16_t> bf(ternary ? 0 : static_cast<size_t>(mt) * 128 * ld, 0);
+        for (int64_t i = 0; i < (ternary ? 0 : n); ++i) {
             const int64_t ti = i / 128, ri = i % 128;
             for (int64_t j = 0; j < n; ++j) {
                 const double v = value_at(hp.dense.data(), hp.jtype, i * n + j);
@@ -462,10 +487,12 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
                 jsum += static_cast<long long>(v);
             }
         }
-        DOCH_CHECK(upload(&c->dense, bf.data(), bf.size() * 2));
-        c->dense_type = ISING_BF16;
-        c->dense_ld = ld;
-        c->dense_jsum = jsum;
+        if (!ternary) {
+            DOCH_CHECK(upload(&c->dense, bf.data(), bf.size() * 2));
+            c->dense_type = ISING_BF16;
+            c->dense_ld = ld;
+            c->dense_jsum = jsum;
+        }
     }
     if (c->has_h) {
         std::vector<float> hf(hp.n);

@@ -83,7 +83,11 @@ struct ising_context {
     // DENSE: integer couplings held as BF16 (exact for |J| <= 256) in the
     // tensor-core tile order [ceil(n/128)][dense_ld/64][128][64], 128-byte
     // swizzled; dense_ld = n rounded up to 64 (zero padded)
+    // dense_ternary: every entry is -1, 0 or +1 and J is held instead as packed
+    // 2-bit codes in the same tile order (2 KB per 128 x 64 tile, row-major,
+    // 4 codes per byte from the low bits: 0 -> 0, 1 -> +1, 2 -> -1)
     void *dense = nullptr;
+    bool dense_ternary = false;
     int dense_type = 0;
     int64_t dense_ld = 0;
     long long dense_jsum = 0;  // sum_ij J_ij, for the cut

@@ -21,7 +21,7 @@
 //
 // Pipeline per CTA (256 threads):
 //   warp 0, one lane: producer. K-block kb (64 columns of J = 64 spins of
-//     X) goes to stage kb % kStages by two cp.async.bulk copies: A tile
+//     X) goes to ring stage it % kStages by two cp.async.bulk copies: A tile
 //     128 x 64 (16 KB), B tile N x 64 (N x 128 B); arrival tracked by the
 //     stage's "full" mbarrier (complete_tx).
 //   warp 1, one lane: MMA issuer. Waits "full", issues four
@@ -50,17 +50,28 @@
 namespace doch {
 namespace {
 
-constexpr int kStages = 4;
+// Ring stages: 4 with BF16 A and B tiles in shared memory (48 KB per stage);
+// 6 in ternary mode, where only B (32 KB) lives in shared memory and A in TMEM.
+template <bool TERN> constexpr int kStagesOf = TERN ? 6 : 4;
 constexpr int kBM = 128;           // rows of J per tile (MMA M)
 constexpr int kBK = 64;            // K per stage: 64 BF16 = 128 bytes = one swizzle row
 constexpr int kThreadsTC = 256;
 constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
 
+constexpr uint32_t kTernTile = kBM * kBK / 4;  // bytes of one packed ternary J tile (2 bits per entry)
+constexpr int kJStages = 8;                      // packed ternary tiles staged ahead
+
+template <bool TERN>
 struct DenseSmem {
-    alignas(1024) unsigned char a[kStages][kBM * kBK * 2];
-    alignas(1024) unsigned char b[kStages][256 * kBK * 2];
-    alignas(8) unsigned long long full[kStages];
-    alignas(8) unsigned long long empty[kStages];
+    static constexpr int kS = kStagesOf<TERN>;
+    alignas(1024) unsigned char b[kS][256 * kBK * 2];
+    alignas(1024) unsigned char a[TERN ? 1 : kS][TERN ? 1024 : kBM * kBK * 2];  // BF16 A tiles (unused if ternary)
+    alignas(16) unsigned char jp[kJStages][kTernTile];  // packed ternary J (ternary mode)
+    alignas(8) unsigned long long full[kS];             // B (and BF16 A) landed
+    alignas(8) unsigned long long empty[kS];            // MMAs of the stage done
+    alignas(8) unsigned long long conv[kS];             // ternary: A tile expanded
+    alignas(8) unsigned long long jfull[kJStages];      // ternary: packed tile landed
+    alignas(8) unsigned long long jempty[kJStages];     // ternary: packed tile read
     alignas(8) unsigned long long acc_ready;
     uint32_t tmem_base;
     int abort_flag;
@@ -95,6 +106,23 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t pari
         : "r"(saddr(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// bounded wait for a long phase (the accumulator): polls every ~0.5 us so the
+// waiting warps leave the issue slots to the producer, MMA and converter threads
+__device__ __forceinline__ bool mbar_wait_idle(unsigned long long *bar, uint32_t parity, int *err,
+                                               volatile int *abort_flag) {
+    const uint64_t t0 = gtime();
+    while (!mbar_test(bar, parity)) {
+        if (*abort_flag) return false;
+        if (gtime() - t0 > kWaitNs) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+        __nanosleep(500);
+    }
+    return true;
 }
 
 // bounded wait on a phase parity; false (and the error word set) on timeout
@@ -155,6 +183,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// the same MMA with A read from tensor memory (rows in lanes, two BF16 per 32-bit column)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive 32-bit columns of this warp's 32 TMEM lanes from registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_commit(unsigned long long *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                  : "memory");
@@ -177,22 +230,40 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// BF16 bits of a 2-bit ternary code: 0 -> 0, 1 -> +1, 2 -> -1 (3 unused -> 0)
+__device__ __forceinline__ uint32_t tern_bf16(uint32_t code) {
+    return code == 1 ? 0x3F80u : (code == 2 ? 0xBF80u : 0u);
+}
+
 // MODE 0: DOCH step into Xt_out. MODE 1: energy partials q_r into q_out (int64).
-template <int MODE>
+// TERN: J is stored as packed 2-bit codes (entries in {-1, 0, +1}); warps 4-7
+// expand each K block into BF16 and store it in tensor memory (columns a_col +
+// 32 s for stage s), from where the MMA reads A; shared memory then carries
+// only the B tiles, the packed codes and the barriers.
+template <int MODE, bool TERN>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__restrict__ xt_in,
+dense_tc_kernel(const void *__restrict__ jt, const __nv_bfloat16 *__restrict__ xt_in,
                 __nv_bfloat16 *__restrict__ xt_out, const float *__restrict__ h, int n, int kblocks, int R,
-                int R_pad, int n_tile, uint32_t tmem_cols, float alpha, float zscale, float xscale,
+                int R_pad, int n_tile, uint32_t tmem_cols, uint32_t a_col, float alpha, float zscale,
+                float xscale,
                 long long *__restrict__ q_out, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(
+    __shared__ uint32_t lut[16];  // ternary: two 2-bit codes -> two BF16
+    using Smem = DenseSmem<TERN>;
+    constexpr int kStages = Smem::kS;
+    Smem &sm = *reinterpret_cast<Smem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
     const int r0 = blockIdx.y * n_tile;
-    constexpr uint32_t a_bytes = kBM * kBK * 2;
+    // bytes of J per K block: a BF16 tile, or a packed ternary tile expanded on chip
+    constexpr uint32_t a_bytes = TERN ? kTernTile : kBM * kBK * 2;
     const uint32_t b_bytes = static_cast<uint32_t>(n_tile) * kBK * 2;
-    const __nv_bfloat16 *a_src = jt + static_cast<size_t>(blockIdx.x) * kblocks * (kBM * kBK);
+    const unsigned char *a_src = static_cast<const unsigned char *>(jt) + static_cast<size_t>(blockIdx.x) * kblocks * a_bytes;
     const __nv_bfloat16 *b_src = xt_in + static_cast<size_t>(r0) * kBK;
     volatile int *abort_flag = &sm.abort_flag;
 
@@ -202,9 +273,16 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
             mbar_init(&sm.empty[s], 1);
         }
         mbar_init(&sm.acc_ready, 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&sm.conv[s], 128);
+        for (int p = 0; p < kJStages; ++p) {
+            mbar_init(&sm.jfull[p], 1);
+            mbar_init(&sm.jempty[p], 128);
+        }
         sm.abort_flag = 0;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (TERN && threadIdx.x < 16)
+        lut[threadIdx.x] = tern_bf16(threadIdx.x & 3) | (tern_bf16(threadIdx.x >> 2) << 16);
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sm.tmem_base)),
                      "r"(tmem_cols)
@@ -216,7 +294,7 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sm.tmem_base;
 
-    int issued = 0;  // producer: K-blocks whose copies were issued
+    int issued = 0;  // producers: K-blocks whose copies were issued
     // Each CTA walks K from its own starting block kb0 and wraps around, so at
     // any moment the CTAs stream different parts of J (equal 4 MB-aligned
     // offsets in lockstep would queue on the same DRAM channels) and read
@@ -228,8 +306,12 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
             int kb = kb0 + it;
             if (kb >= kblocks) kb -= kblocks;
             if (it >= kStages && !mbar_wait(&sm.empty[s], ((it / kStages) - 1) & 1, err, abort_flag)) break;
-            mbar_expect_tx(&sm.full[s], a_bytes + b_bytes);
-            bulk_load(sm.a[s], a_src + static_cast<size_t>(kb) * (kBM * kBK), a_bytes, &sm.full[s]);
+            if (TERN) {
+                mbar_expect_tx(&sm.full[s], b_bytes);
+            } else {
+                mbar_expect_tx(&sm.full[s], a_bytes + b_bytes);
+                bulk_load(sm.a[s], a_src + static_cast<size_t>(kb) * a_bytes, a_bytes, &sm.full[s]);
+            }
             bulk_load(sm.b[s], b_src + static_cast<size_t>(kb) * R_pad * kBK, b_bytes, &sm.full[s]);
             issued = it + 1;
         }
@@ -238,13 +320,21 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
         bool ok = true;
         for (int it = 0; it < kblocks; ++it) {
             const int s = it % kStages;
-            if (!mbar_wait(&sm.full[s], (it / kStages) & 1, err, abort_flag)) { ok = false; break; }
+            // ternary: A is ready when the converters arrived on conv[s]; B when full[s] completed
+            if ((TERN && !mbar_wait(&sm.conv[s], (it / kStages) & 1, err, abort_flag)) ||
+                !mbar_wait(&sm.full[s], (it / kStages) & 1, err, abort_flag)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t ad = smem_desc_sw128(sm.a[s]);
             const uint64_t bd = smem_desc_sw128(sm.b[s]);
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k)  // K = 16 per MMA: +32 bytes = +2 in the descriptor
-                mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (it | k) != 0);
+                if (TERN)  // K = 16 BF16 = 8 TMEM columns per MMA
+                    mma_bf16_ta(tmem, tmem + a_col + 32 * s + 8 * k, bd + 2 * k, idesc, (it | k) != 0);
+                else
+                    mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (it | k) != 0);
             mma_commit(&sm.empty[s]);
         }
         // the accumulator barrier also tracks completion of every MMA issued so far
@@ -254,6 +344,41 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
             while (!mbar_test(&sm.acc_ready, 0) && gtime() - t0 < kWaitNs) {
             }
         }
+    } else if (TERN && warp == 3 && lane == 0) {
+        // producer of the packed ternary tiles (2 KB each), kJStages ahead
+        for (int it = 0; it < kblocks; ++it) {
+            const int p = it % kJStages;
+            int kb = kb0 + it;
+            if (kb >= kblocks) kb -= kblocks;
+            if (it >= kJStages && !mbar_wait(&sm.jempty[p], ((it / kJStages) - 1) & 1, err, abort_flag)) break;
+            mbar_expect_tx(&sm.jfull[p], a_bytes);
+            bulk_load(sm.jp[p], a_src + static_cast<size_t>(kb) * a_bytes, a_bytes, &sm.jfull[p]);
+            issued = it + 1;
+        }
+    } else if (TERN && warp >= 4) {
+        // Converters: thread t expands row t of each K block, 64 codes (16 bytes)
+        // into 32 columns of two BF16 each and stores them in its TMEM lane t,
+        // once the packed tile has landed and the MMAs freed the A stage. The
+        // waits are made warp-uniform: tcgen05.st is a .sync.aligned instruction.
+        const int t = threadIdx.x - 128;
+        const uint32_t a_lane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + a_col;
+        for (int it = 0; it < kblocks; ++it) {
+            const int s = it % kStages, p = it % kJStages;
+            if (!__all_sync(0xffffffffu, mbar_wait(&sm.jfull[p], (it / kJStages) & 1, err, abort_flag))) break;
+            const uint4 codes = *reinterpret_cast<const uint4 *>(sm.jp[p] + 16 * t);
+            mbar_arrive(&sm.jempty[p]);
+            if (it >= kStages &&
+                !__all_sync(0xffffffffu, mbar_wait(&sm.empty[s], ((it / kStages) - 1) & 1, err, abort_flag)))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t words[4] = {codes.x, codes.y, codes.z, codes.w};
+            uint32_t v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = lut[(words[j >> 3] >> (4 * (j & 7))) & 15];
+            tmem_st32(a_lane + 32 * s, v);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&sm.conv[s]);
+        }
     }
     __syncwarp();
     // Epilogue, all eight warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its
@@ -262,7 +387,7 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
         const int q = warp & 3, half = warp >> 2;
         const int row = m0 + 32 * q + lane;
         // warp-uniform decision: tcgen05.ld below is a .sync.aligned warp instruction
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.acc_ready, 0, err, abort_flag) && !*abort_flag);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_idle(&sm.acc_ready, 0, err, abort_flag) && !*abort_flag);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float hv = (h && row < n) ? h[row] : 0.f;
@@ -307,6 +432,13 @@ dense_tc_kernel(const __nv_bfloat16 *__restrict__ jt, const __nv_bfloat16 *__res
         for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
             const uint64_t t0 = gtime();
             while (!mbar_test(&sm.full[it % kStages], (it / kStages) & 1) && gtime() - t0 < kWaitNs) {
+            }
+        }
+    }
+    if (TERN && warp == 3 && lane == 0 && *abort_flag) {
+        for (int it = (issued > kJStages ? issued - kJStages : 0); it < issued; ++it) {
+            const uint64_t t0 = gtime();
+            while (!mbar_test(&sm.jfull[it % kJStages], (it / kJStages) & 1) && gtime() - t0 < kWaitNs) {
             }
         }
     }
@@ -392,7 +524,7 @@ __global__ void dense_energy_finish(const long long *__restrict__ q, const long 
 
 struct DenseGeom {
     int n, kblocks, R, R_pad, n_tile, m_tiles, r_tiles;
-    uint32_t tmem_cols;
+    uint32_t tmem_cols, a_col;  // TMEM columns allocated; first column of the A stages (ternary)
 };
 
 DenseGeom geometry(const ising_context *c, int R) {
@@ -406,22 +538,31 @@ DenseGeom geometry(const ising_context *c, int R) {
     g.r_tiles = g.R_pad / g.n_tile;
     uint32_t cols = 32;
     while (cols < static_cast<uint32_t>(g.n_tile)) cols <<= 1;
+    g.a_col = cols;
+    if (c->dense_ternary) {  // + one 32-column A tile per stage, rounded up to a power of two
+        cols += kStagesOf<true> * 32;
+        uint32_t p2 = 32;
+        while (p2 < cols) p2 <<= 1;
+        cols = p2;
+    }
     g.tmem_cols = cols;
     return g;
 }
 
-size_t smem_bytes() { return sizeof(DenseSmem) + 1024; }
+template <bool TERN>
+size_t smem_bytes() { return sizeof(DenseSmem<TERN>) + 1024; }
 
 template <int MODE>
 ising_status_t launch_dense(const ising_context *c, const DenseGeom &g, const __nv_bfloat16 *xt_in,
                             __nv_bfloat16 *xt_out, const float *h, float alpha, float zscale, float xscale,
                             long long *q_out, cudaStream_t st) {
-    auto kern = dense_tc_kernel<MODE>;
-    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes())));
+    auto kern = c->dense_ternary ? dense_tc_kernel<MODE, true> : dense_tc_kernel<MODE, false>;
+    const size_t smem = c->dense_ternary ? smem_bytes<true>() : smem_bytes<false>();
+    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     dim3 grid(static_cast<unsigned>(g.m_tiles), static_cast<unsigned>(g.r_tiles));
-    kern<<<grid, kThreadsTC, smem_bytes(), st>>>(static_cast<const __nv_bfloat16 *>(c->dense), xt_in, xt_out, h, g.n,
-                                                 g.kblocks, g.R, g.R_pad, g.n_tile, g.tmem_cols, alpha, zscale,
-                                                 xscale, q_out, c->err_word);
+    kern<<<grid, kThreadsTC, smem, st>>>(c->dense, xt_in, xt_out, h, g.n,
+                                                 g.kblocks, g.R, g.R_pad, g.n_tile, g.tmem_cols, g.a_col, alpha,
+                                                 zscale, xscale, q_out, c->err_word);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

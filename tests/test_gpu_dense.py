@@ -14,6 +14,8 @@ same BF16-rounded x0.
     own energies).
   * Energies and cuts of a given spin vector are exact integers (J S
     accumulates exactly in FP32 for integer J with |J| <= 256): bit for bit.
+Couplings in {-1, 0, +1} take the packed ternary storage (expanded on chip);
+other integer couplings the BF16 storage; both are tested.
 """
 import numpy as np
 import pytest
@@ -36,6 +38,20 @@ def lib():
     return N.load()
 
 
+def _jmat(kind, n, seed):
+    """Symmetric integer couplings with zero diagonal: "pm1" (dense +-1, held as packed
+    ternary codes), "pm1_sparse" (+-1 with about half the pairs zero, ternary) or "int"
+    (|J| in 1..3, held as BF16)."""
+    J = I.dense_pm1(n, seed=seed).astype(np.int64)
+    if kind == "pm1":
+        return J.astype(np.int8)
+    u = np.triu(I.x0_uniform(n, n, seed=seed + 1), 1)
+    u = u + u.T
+    if kind == "pm1_sparse":
+        return (J * (np.abs(u) >= 0.5)).astype(np.int8)
+    return (J * (1 + np.floor(3 * np.abs(u)).clip(0, 2))).astype(np.int8)
+
+
 def _bf16(x):
     t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16)
     return t, t.float().numpy().astype(np.float64)
@@ -51,9 +67,11 @@ def _bf16_ulp(v):
     return 2.0 ** (e - 7)
 
 
-@pytest.mark.parametrize("n, R", [(256, 32), (200, 20), (130, 5), (384, 256)])
-def test_dense_iterates_bf16(n, R):
-    J = I.dense_pm1(n, seed=91)
+@pytest.mark.parametrize("n, R, kind", [(256, 32, "pm1"), (200, 20, "pm1"), (130, 5, "pm1"), (384, 256, "pm1"),
+                                        (256, 32, "int"), (200, 20, "int"), (384, 256, "int"),
+                                        (200, 20, "pm1_sparse"), (384, 48, "pm1_sparse")])
+def test_dense_iterates_bf16(n, R, kind):
+    J = _jmat(kind, n, 91)
     P = O.Problem(J)
     alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
     xt, x0 = _bf16(I.x0_uniform(n, R, seed=92))
@@ -82,9 +100,10 @@ def test_dense_iterates_bf16(n, R):
         N.ising_destroy(h)
 
 
-@pytest.mark.parametrize("n, R", [(300, 40), (128, 1), (520, 257)])
-def test_dense_energy_exact(n, R):
-    J = I.dense_pm1(n, seed=93)
+@pytest.mark.parametrize("n, R, kind", [(300, 40, "pm1"), (128, 1, "pm1"), (520, 257, "pm1"),
+                                        (300, 40, "int"), (520, 257, "int"), (300, 40, "pm1_sparse")])
+def test_dense_energy_exact(n, R, kind):
+    J = _jmat(kind, n, 93)
     hf = (np.round(3 * I.field_gauss(n, 1.0, seed=94))).astype(np.int8)
     x = I.x0_uniform(n, R, seed=95)
     x[::7] = 0.0
