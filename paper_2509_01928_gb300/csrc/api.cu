@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "cbrt.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -383,6 +384,9 @@ void destroy_ctx(ising_context *c) {
     cudaFree(c->err_word);
     if (c->err_host) cudaFreeHost(c->err_host);
     cudaFree(c->batch_order);
+    cudaFree(c->ell_col);
+    cudaFree(c->ell_val);
+    cudaFree(c->ell_off);
     cudaFree(c->batch_queue);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -393,6 +397,7 @@ void destroy_ctx(ising_context *c) {
     c->params.release();
     c->ckpt.release();
     c->work.release();
+    c->batch_items.release();
     delete c;
 }
 
@@ -415,6 +420,8 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
         std::vector<int64_t> work(hp.n_inst);
         for (int b = 0; b < hp.n_inst; ++b)
             work[b] = (hp.off[b + 1] - hp.off[b]) + (hp.row_ptr[hp.off[b + 1]] - hp.row_ptr[hp.off[b]]);
+        c->inst_nnz_h.resize(hp.n_inst);
+        for (int b = 0; b < hp.n_inst; ++b) c->inst_nnz_h[b] = hp.row_ptr[hp.off[b + 1]] - hp.row_ptr[hp.off[b]];
         std::vector<int32_t> order(hp.n_inst);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
@@ -429,6 +436,34 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
             c->max_row_nnz = std::max(c->max_row_nnz, hp.row_ptr[i + 1] - hp.row_ptr[i]);
         DOCH_CHECK(upload(&c->row_ptr, hp.row_ptr.data(), sizeof(int64_t) * hp.row_ptr.size()));
         DOCH_CHECK(upload(&c->col, hp.col.data(), sizeof(int32_t) * hp.col.size()));
+        if (hp.n_inst > 1 && c->max_inst_n <= 65536) {
+            // transposed ELL copy for the shared-memory resident batched kernel
+            std::vector<int64_t> eoff(hp.n_inst + 1, 0);
+            c->ell_deg_h.assign(hp.n_inst, 0);
+            for (int b = 0; b < hp.n_inst; ++b) {
+                int d = 0;
+                for (int64_t i = hp.off[b]; i < hp.off[b + 1]; ++i)
+                    d = std::max<int>(d, static_cast<int>(hp.row_ptr[i + 1] - hp.row_ptr[i]));
+                c->ell_deg_h[b] = d;
+                eoff[b + 1] = eoff[b] + static_cast<int64_t>(d) * (hp.off[b + 1] - hp.off[b]);
+            }
+            std::vector<uint16_t> ec(eoff.back());
+            std::vector<float> ev(eoff.back());
+            for (int b = 0; b < hp.n_inst; ++b) {
+                const int64_t lo = hp.off[b], nb = hp.off[b + 1] - lo;
+                for (int64_t i = 0; i < nb; ++i) {
+                    const int64_t e0 = hp.row_ptr[lo + i], cnt = hp.row_ptr[lo + i + 1] - e0;
+                    for (int k = 0; k < c->ell_deg_h[b]; ++k) {
+                        const size_t at = static_cast<size_t>(eoff[b] + k * nb + i);
+                        ec[at] = static_cast<uint16_t>(k < cnt ? hp.col[e0 + k] - lo : i);
+                        ev[at] = k < cnt ? static_cast<float>(hp.val[e0 + k]) : 0.f;
+                    }
+                }
+            }
+            DOCH_CHECK(upload(&c->ell_col, ec.data(), sizeof(uint16_t) * ec.size()));
+            DOCH_CHECK(upload(&c->ell_val, ev.data(), sizeof(float) * ev.size()));
+            DOCH_CHECK(upload(&c->ell_off, eoff.data(), sizeof(int64_t) * eoff.size()));
+        }
         if (hp.jtype == ISING_I16) {  // held as I32 on the device
             std::vector<int32_t> v(hp.val.size());
             for (size_t e = 0; e < v.size(); ++e) v[e] = static_cast<int32_t>(hp.val[e]);
@@ -534,14 +569,21 @@ ising_status_t upload_params(ising_context *c, const double *alpha, int alpha_le
         if (!std::isfinite(v)) return fail(ISING_ERR_NONFINITE, "beta is not finite");
         if (v <= 0.0) return fail(ISING_ERR_INVALID_ARG, "beta must be > 0");
     }
-    // layout: alpha_d | beta_d | alpha_f | inv_beta_f (each 256-byte aligned)
+    // layout: alpha_d | beta_d | alpha_f | inv_beta_f | zscale_f | xscale_f (each 256-byte aligned)
     auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
-    const size_t o1 = al(na * 8), o2 = o1 + al(ni * 8), o3 = o2 + al(na * 4), tot = o3 + al(ni * 4);
+    const size_t o1 = al(na * 8), o2 = o1 + al(ni * 8), o3 = o2 + al(na * 4), o4 = o3 + al(ni * 4),
+                 o5 = o4 + al(ni * 4), tot = o5 + al(ni * 4);
     std::vector<unsigned char> host(tot);
     std::memcpy(host.data(), a.data(), na * 8);
     std::memcpy(host.data() + o1, b.data(), ni * 8);
     for (size_t i = 0; i < na; ++i) reinterpret_cast<float *>(host.data() + o2)[i] = static_cast<float>(a[i]);
-    for (int i = 0; i < ni; ++i) reinterpret_cast<float *>(host.data() + o3)[i] = static_cast<float>(1.0 / b[i]);
+    for (int i = 0; i < ni; ++i) {
+        const double ib = 1.0 / b[i];
+        const int k = cbrt_prescale_exp(ib);
+        reinterpret_cast<float *>(host.data() + o3)[i] = static_cast<float>(ib);
+        reinterpret_cast<float *>(host.data() + o4)[i] = static_cast<float>(std::ldexp(ib, 3 * k));
+        reinterpret_cast<float *>(host.data() + o5)[i] = std::ldexp(1.0f, -k);
+    }
     DOCH_CHECK(c->params.ensure(tot));
     DOCH_CUDA(cudaMemcpyAsync(c->params.ptr, host.data(), tot, cudaMemcpyHostToDevice, st));
     // the source is pageable: make sure the copy has consumed it
@@ -551,6 +593,8 @@ ising_status_t upload_params(ising_context *c, const double *alpha, int alpha_le
     out.beta_d = reinterpret_cast<const double *>(base + o1);
     out.alpha_f = reinterpret_cast<const float *>(base + o2);
     out.inv_beta_f = reinterpret_cast<const float *>(base + o3);
+    out.zscale_f = reinterpret_cast<const float *>(base + o4);
+    out.xscale_f = reinterpret_cast<const float *>(base + o5);
     out.alpha_len = alpha_len;
     return ISING_OK;
 }
@@ -636,6 +680,9 @@ ising_status_t tune_batched(ising_context *c, const float *x, int R, const Param
 // buffers, parameters and shape stay the same.
 ising_status_t batched_iterate(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
                                cudaStream_t st) {
+    // every (instance, replica group) resident in shared memory when they fit
+    const ising_status_t rs = batched_resident_launch(c, x, R, p, iters, st);
+    if (rs != ISING_ERR_UNSUPPORTED) return rs;
     BatchedConfig cfg;
     DOCH_CHECK(tune_batched(c, x, R, p, st, &cfg));
     const size_t xbytes = static_cast<size_t>(c->n) * R * sizeof(float);

@@ -110,6 +110,22 @@ struct ising_context {
     int32_t *batch_order = nullptr;
     int *batch_queue = nullptr;
     std::map<int, doch::BatchedConfig> batch_tuned;  // by R
+    // shared-memory resident kernel: per-instance nnz (host), work items
+    // (instance, first replica, G) for batch_items_R replicas, their shared memory
+    std::vector<int64_t> inst_nnz_h;
+    // transposed ELL copy of batched instances of at most 65536 spins: per
+    // instance b, ell_deg[b] slots (the largest row degree) x n_b rows from
+    // entry ell_off[b], slot k of row i at ell_off[b] + k n_b + i; 16-bit
+    // instance-local columns, FP32 weights; a row's entries in CSR order,
+    // padded with (i, 0)
+    uint16_t *ell_col = nullptr;
+    float *ell_val = nullptr;
+    int64_t *ell_off = nullptr;
+    std::vector<int> ell_deg_h;
+    doch::DevBuf batch_items;
+    int batch_items_R = 0;
+    int batch_items_count = 0;
+    size_t batch_items_smem = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<uintptr_t> batch_key;
@@ -140,6 +156,10 @@ struct ParamTabs {
     const double *beta_d = nullptr;
     const float *alpha_f = nullptr;
     const float *inv_beta_f = nullptr;
+    // per instance, for the prescaled fast cube root: cbrt(z / beta) =
+    // cbrt(z * zscale) * xscale with zscale = 2^(3k) / beta, xscale = 2^-k
+    const float *zscale_f = nullptr;
+    const float *xscale_f = nullptr;
     int alpha_len = 1;
 };
 
@@ -168,6 +188,11 @@ ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, in
 
 // Batched persistent kernel (k_batched.cu): FP32 iterates, ping-pong xa <-> xb;
 // after `iters` steps the result is in xa (iters even) or xb (odd).
+// Batched instances with each (instance, replica group) resident in shared
+// memory for all steps (k_batched.cu); ISING_ERR_UNSUPPORTED when an instance
+// does not fit or x is not 16-byte aligned. Updates x in place.
+ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
+                                       cudaStream_t st);
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
                               const ParamTabs &p, int iters, cudaStream_t st);
 

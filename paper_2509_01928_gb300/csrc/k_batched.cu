@@ -10,7 +10,14 @@
 // of V replicas) items, so each CSR entry is read once per V replicas and
 // each neighbour gather is a V-wide vector. The iterate lives in two global
 // buffers (L2-resident per instance); loads of x use coherent global loads
-// because the same launch writes it.
+// because the same launch writes it. Gather indices are 32-bit element
+// indices into the iterate viewed as [n][R/V] V-vectors (n R / V < 2^31 is
+// checked on the host). The cube root is the prescaled base-2 form
+// cbrt(z zscale_b) xscale_b with the instance's power-of-two prescale.
+#include <algorithm>
+#include <vector>
+
+#include "cbrt.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -24,22 +31,20 @@ template <> struct FV<2> { using type = float2; };
 template <> struct FV<4> { using type = float4; };
 
 template <int V>
-__device__ __forceinline__ void ldx(const float *p, float (&v)[V]) {
-    using T = typename FV<V>::type;
-    const T w = *reinterpret_cast<const T *>(p);  // coherent: x is written in this launch
+__device__ __forceinline__ void ldx(const typename FV<V>::type *p, float (&v)[V]) {
+    const typename FV<V>::type w = *p;  // coherent: x is written in this launch
     const float *q = reinterpret_cast<const float *>(&w);
 #pragma unroll
     for (int k = 0; k < V; ++k) v[k] = q[k];
 }
 
 template <int V>
-__device__ __forceinline__ void stx(float *p, const float (&v)[V]) {
-    using T = typename FV<V>::type;
-    T w;
+__device__ __forceinline__ void stx(typename FV<V>::type *p, const float (&v)[V]) {
+    typename FV<V>::type w;
     float *q = reinterpret_cast<float *>(&w);
 #pragma unroll
     for (int k = 0; k < V; ++k) q[k] = v[k];
-    *reinterpret_cast<T *>(p) = w;
+    *p = w;
 }
 
 template <typename VT, int V>
@@ -48,7 +53,9 @@ __global__ void batched_persistent(float *xa, float *xb,
                                    const VT *__restrict__ val, const float *__restrict__ h,
                                    const int64_t *__restrict__ off, const int32_t *__restrict__ order,
                                    int n_inst, int R, const float *__restrict__ alpha_tab, int alpha_len,
-                                   const float *__restrict__ inv_beta_tab, int iters, int *__restrict__ queue) {
+                                   const float *__restrict__ zscale_tab, const float *__restrict__ xscale_tab,
+                                   int iters, int *__restrict__ queue) {
+    using T = typename FV<V>::type;
     __shared__ int next;
     const int C = R / V;
     // each thread keeps one replica chunk and strides over rows: no division in the loop
@@ -64,10 +71,10 @@ __global__ void batched_persistent(float *xa, float *xb,
         if (w >= n_inst) break;
         const int b = __ldg(order + w);
         const int64_t lo = __ldg(off + b), hi = __ldg(off + b + 1);
-        const float ib = __ldg(inv_beta_tab + b);
+        const float zs = __ldg(zscale_tab + b), xsc = __ldg(xscale_tab + b);
         for (int k = 0; k < iters; ++k) {
-            const float *xi = (k & 1) ? xb : xa;
-            float *xo = (k & 1) ? xa : xb;
+            const T *xi = reinterpret_cast<const T *>((k & 1) ? xb : xa) + ch;
+            T *xo = reinterpret_cast<T *>((k & 1) ? xa : xb) + ch;
             const float a = __ldg(alpha_tab + static_cast<int64_t>(b) * alpha_len + (alpha_len == 1 ? 0 : k));
             for (int64_t i = lo + row0; i < hi && active; i += rows_step) {
                 float acc[V];
@@ -88,7 +95,7 @@ __global__ void batched_persistent(float *xa, float *xb,
                     float xv[kBatch][V];
 #pragma unroll
                     for (int q = 0; q < kBatch; ++q)
-                        if (q < cnt) ldx<V>(xi + static_cast<int64_t>(js[q]) * R + ch * V, xv[q]);
+                        if (q < cnt) ldx<V>(xi + js[q] * C, xv[q]);
 #pragma unroll
                     for (int q = 0; q < kBatch; ++q)
                         if (q < cnt) {
@@ -97,11 +104,12 @@ __global__ void batched_persistent(float *xa, float *xb,
                         }
                 }
                 float xs[V], out[V];
-                ldx<V>(xi + i * R + ch * V, xs);
+                const int ic = static_cast<int>(i) * C;
+                ldx<V>(xi + ic, xs);
                 const float hi_ = h ? __ldg(h + i) : 0.f;
 #pragma unroll
-                for (int q = 0; q < V; ++q) out[q] = cbrtf((acc[q] + a * xs[q] + hi_) * ib);
-                stx<V>(xo + i * R + ch * V, out);
+                for (int q = 0; q < V; ++q) out[q] = cbrt_pow2((acc[q] + a * xs[q] + hi_) * zs) * xsc;
+                stx<V>(xo + ic, out);
             }
             __syncthreads();
         }
@@ -112,6 +120,8 @@ template <typename VT, int V>
 ising_status_t launch_b(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
                         const ParamTabs &p, int iters, cudaStream_t st) {
     if (R / V > cfg.threads) return ISING_ERR_UNSUPPORTED;  // a CTA must hold one row's chunks
+    if (c->n * (R / V) >= (int64_t(1) << 31))
+        return fail(ISING_ERR_UNSUPPORTED, "batched: n R / V must be below 2^31 (32-bit gather indices)");
     auto kern = batched_persistent<VT, V>;
     cudaFuncAttributes attr;
     DOCH_CUDA(cudaFuncGetAttributes(&attr, kern));
@@ -125,7 +135,7 @@ ising_status_t launch_b(const ising_context *c, const BatchedConfig &cfg, float 
     DOCH_CUDA(cudaMemsetAsync(c->batch_queue, 0, sizeof(int), st));
     kern<<<grid, cfg.threads, 0, st>>>(xa, xb, c->row_ptr, c->col, static_cast<const VT *>(c->val), c->h_f32,
                                        c->inst_off, c->batch_order, c->n_inst, R, p.alpha_f, p.alpha_len,
-                                       p.inv_beta_f, iters, c->batch_queue);
+                                       p.zscale_f, p.xscale_f, iters, c->batch_queue);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
@@ -142,7 +152,198 @@ ising_status_t dispatch_b(const ising_context *c, const BatchedConfig &cfg, floa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory resident variant. A work item is (instance b, replicas g0 ..
+// g0+G-1); one CTA runs all steps of an item with both Jacobi copies of that
+// slice of the iterate in shared memory ([n_b][G] floats each), so every
+// neighbour gather is a G-wide shared-memory load and only the couplings are
+// re-read (from L2) each step, from the transposed ELL copy: slot k of rows
+// i .. i+31 is 32 consecutive entries, one coalesced load per warp. G is chosen per instance, the largest power of
+// two dividing R with 2 n_b G floats fitting the CTA's shared memory. Items
+// are queued longest first; the iterate is updated in place in global memory
+// at the end of the item (items own disjoint slices).
+
+template <int G>
+__device__ __forceinline__ void ldg_vec(const float *p, float (&v)[G]) {
+    if constexpr (G >= 4) {
+#pragma unroll
+        for (int c = 0; c < G / 4; ++c) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[c];
+            v[4 * c] = t.x; v[4 * c + 1] = t.y; v[4 * c + 2] = t.z; v[4 * c + 3] = t.w;
+        }
+    } else if constexpr (G == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[G]) {
+    if constexpr (G >= 4) {
+#pragma unroll
+        for (int c = 0; c < G / 4; ++c)
+            reinterpret_cast<float4 *>(p)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    } else if constexpr (G == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int64_t lo, int nb, int g0, int D,
+                                              const uint16_t *__restrict__ ecol, const float *__restrict__ eval,
+                                              const float *__restrict__ h, const float *__restrict__ alpha_row,
+                                              int alpha_len, float zs, float xsc, int iters, float *s0, float *s1) {
+    const int T = blockDim.x;
+    for (int i = threadIdx.x; i < nb; i += T) {
+        float v[G];
+        ldg_vec<G>(x + (lo + i) * R + g0, v);
+        st_vec<G>(s0 + i * G, v);
+    }
+    __syncthreads();
+    float *cur = s0, *nxt = s1;
+    for (int k = 0; k < iters; ++k) {
+        const float a = __ldg(alpha_row + (alpha_len == 1 ? 0 : k));
+        for (int i = threadIdx.x; i < nb; i += T) {
+            float acc[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) acc[q] = 0.f;
+            // slots in batches of kBatch: the (coalesced) index/weight loads of a batch first,
+            // then the shared-memory gathers and products in CSR order
+            for (int k0 = 0; k0 < D; k0 += kBatch) {
+                const int cnt = D - k0 < kBatch ? D - k0 : kBatch;
+                int js[kBatch];
+                float ws[kBatch];
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    const int at = (k0 + q) * nb + i;  // < D n_b < 2^31 (checked on the host)
+                    js[q] = q < cnt ? static_cast<int>(__ldg(ecol + at)) : 0;
+                    ws[q] = q < cnt ? __ldg(eval + at) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q)
+                    if (q < cnt) {
+                        float xv[G];
+                        ldg_vec<G>(cur + js[q] * G, xv);
+#pragma unroll
+                        for (int r = 0; r < G; ++r) acc[r] += ws[q] * xv[r];
+                    }
+            }
+            float xs[G], out[G];
+            ldg_vec<G>(cur + i * G, xs);
+            const float hv = h ? __ldg(h + lo + i) : 0.f;
+#pragma unroll
+            for (int q = 0; q < G; ++q) out[q] = cbrt_pow2((acc[q] + a * xs[q] + hv) * zs) * xsc;
+            st_vec<G>(nxt + i * G, out);
+        }
+        __syncthreads();
+        float *t = cur; cur = nxt; nxt = t;
+    }
+    for (int i = threadIdx.x; i < nb; i += T) {
+        float v[G];
+        ldg_vec<G>(cur + i * G, v);
+        st_vec<G>(x + (lo + i) * R + g0, v);
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1)
+batched_resident(float *__restrict__ x, const uint16_t *__restrict__ ell_col, const float *__restrict__ ell_val,
+                 const int64_t *__restrict__ ell_off, const float *__restrict__ h, const int64_t *__restrict__ off,
+                 const int4 *__restrict__ items, int n_items, int R, const float *__restrict__ alpha_tab,
+                 int alpha_len, const float *__restrict__ zscale_tab, const float *__restrict__ xscale_tab,
+                 int iters, int *__restrict__ queue) {
+    extern __shared__ float4 res_smem4[];
+    __shared__ int next;
+    while (true) {
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+        __syncthreads();  // also: every thread is done with the previous item's shared memory
+        const int w = next;
+        __syncthreads();
+        if (w >= n_items) break;
+        const int4 it = __ldg(items + w);  // (instance, first replica, G, ELL slots)
+        const int b = it.x;
+        const int64_t lo = __ldg(off + b);
+        const int nb = static_cast<int>(__ldg(off + b + 1) - lo);
+        float *s0 = reinterpret_cast<float *>(res_smem4);
+        float *s1 = s0 + static_cast<size_t>(nb) * it.z;
+        const float *arow = alpha_tab + static_cast<int64_t>(b) * alpha_len;
+        const float zs = __ldg(zscale_tab + b), xsc = __ldg(xscale_tab + b);
+        const int64_t eo = __ldg(ell_off + b);
+        const uint16_t *ec = ell_col + eo;
+        const float *ev = ell_val + eo;
+        switch (it.z) {
+            case 16: resident_item<16>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+            case 8: resident_item<8>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+            case 4: resident_item<4>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+            case 2: resident_item<2>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+            default: resident_item<1>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+        }
+    }
+}
+
+ising_status_t launch_resident(ising_context *c, float *x, int R, const ParamTabs &p, int iters, cudaStream_t st) {
+    auto kern = batched_resident;
+    const int smem = static_cast<int>(c->batch_items_smem);
+    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int occ = 0;
+    DOCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 1024, smem));
+    if (occ < 1) return ISING_ERR_UNSUPPORTED;
+    int grid = c->num_sms * occ;
+    if (grid > c->batch_items_count) grid = c->batch_items_count;
+    DOCH_CUDA(cudaMemsetAsync(c->batch_queue, 0, sizeof(int), st));
+    kern<<<grid, 1024, smem, st>>>(x, c->ell_col, c->ell_val, c->ell_off, c->h_f32, c->inst_off,
+                                   c->batch_items.as<int4>(), c->batch_items_count, R, p.alpha_f, p.alpha_len,
+                                   p.zscale_f, p.xscale_f, iters, c->batch_queue);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
 }  // namespace
+
+// Work items of the resident kernel for R replicas (cached per handle and R);
+// ISING_ERR_UNSUPPORTED when an instance does not fit shared memory even with G = 1.
+static ising_status_t resident_items(ising_context *c, int R) {
+    if (c->batch_items_R == R) return ISING_OK;
+    int dev = 0, optin = 0;
+    DOCH_CUDA(cudaGetDevice(&dev));
+    DOCH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int64_t cap = optin - 64;  // the kernel's static shared memory
+    struct Item { int64_t work; int b, g0, G; };
+    std::vector<Item> items;
+    size_t smem = 0;
+    for (int b = 0; b < c->n_inst; ++b) {
+        const int64_t nb = c->inst_off_h[b + 1] - c->inst_off_h[b];
+        int G = 16;
+        while (G > 1 && (R % G != 0 || 2 * nb * G * 4 > cap)) G >>= 1;
+        if (2 * nb * G * 4 > cap) return ISING_ERR_UNSUPPORTED;
+        if (static_cast<int64_t>(c->ell_deg_h[b]) * nb >= (int64_t(1) << 31)) return ISING_ERR_UNSUPPORTED;
+        smem = std::max(smem, static_cast<size_t>(2 * nb * G * 4));
+        for (int g0 = 0; g0 < R; g0 += G) items.push_back({(nb + c->inst_nnz_h[b]) * G, b, g0, G});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &u, const Item &v) { return u.work > v.work; });
+    std::vector<int4> host(items.size());
+    for (size_t i = 0; i < items.size(); ++i)
+        host[i] = make_int4(items[i].b, items[i].g0, items[i].G, c->ell_deg_h[items[i].b]);
+    DOCH_CHECK(c->batch_items.ensure(sizeof(int4) * host.size()));
+    DOCH_CUDA(cudaMemcpy(c->batch_items.ptr, host.data(), sizeof(int4) * host.size(), cudaMemcpyHostToDevice));
+    c->batch_items_count = static_cast<int>(host.size());
+    c->batch_items_smem = std::max<size_t>(smem, 16);
+    c->batch_items_R = R;
+    return ISING_OK;
+}
+
+ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
+                                       cudaStream_t st) {
+    if (!c->batch_queue || !c->ell_col || c->inst_nnz_h.size() != static_cast<size_t>(c->n_inst))
+        return ISING_ERR_UNSUPPORTED;
+    if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return ISING_ERR_UNSUPPORTED;
+    const ising_status_t s = resident_items(c, R);
+    if (s != ISING_OK) return s;
+    return launch_resident(c, x, R, p, iters, st);
+}
 
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
                               const ParamTabs &p, int iters, cudaStream_t st) {
