@@ -249,6 +249,46 @@ def test_csr_batched_uneven_with_field(xdtype, jdtype):
         _close(xg[off[b]:off[b + 1]], ref, TOL32 if xdtype == np.float32 else TOL64)
 
 
+@pytest.mark.parametrize("R", [16, 6])
+def test_csr_batched_resident_group_widths(R):
+    """Instance sizes that take every replica-group width of the shared-memory
+    resident kernel (R = 16: G = 16, 8, 4, 2, 1; R = 6: G = 2, 1)."""
+    sizes, degrees = [400, 3000, 6000, 12000, 20000], [4, 9, 3, 10, 6]
+    gs, hs, J, h, off = _batch(sizes, degrees, seed=60)
+    J.val = J.val.astype(np.float32)
+    h = h.astype(np.float32)
+    x0 = I.x0_uniform(int(off[-1]), R, seed=61)
+    alphas, betas = zip(*[O.alpha_beta(g, eta=1.0, method="wigner") for g in gs])
+    iters = 12
+    with Handle(J, h, off) as hd:
+        x = _dev(x0)
+        N.ising_iterate(hd, x, list(alphas), list(betas), iters, n_instances=len(gs))
+        xg = x.cpu().numpy()
+    for b, g in enumerate(gs):
+        ref = O.doch(O.Problem(g, hs[b].astype(np.float32)), x0[off[b]:off[b + 1]], alphas[b], betas[b], iters)
+        _close(xg[off[b]:off[b + 1]], ref, TOL32)
+
+
+def test_csr_batched_large_instance_global_kernel():
+    """An instance whose two iterate copies exceed shared memory (n = 30000) runs
+    the global-memory persistent kernel, in the same call as a small one."""
+    sizes, degrees = [30000, 700], [3, 5]
+    gs, hs, J, h, off = _batch(sizes, degrees, seed=62)
+    J.val = J.val.astype(np.float32)
+    h = h.astype(np.float32)
+    R = 4
+    x0 = I.x0_uniform(int(off[-1]), R, seed=63)
+    alphas, betas = zip(*[O.alpha_beta(g, eta=1.0, method="wigner") for g in gs])
+    iters = 15
+    with Handle(J, h, off) as hd:
+        x = _dev(x0)
+        N.ising_iterate(hd, x, list(alphas), list(betas), iters, n_instances=len(gs))
+        xg = x.cpu().numpy()
+    for b, g in enumerate(gs):
+        ref = O.doch(O.Problem(g, hs[b].astype(np.float32)), x0[off[b]:off[b + 1]], alphas[b], betas[b], iters)
+        _close(xg[off[b]:off[b + 1]], ref, TOL32)
+
+
 # ---------------------------------------------------------------------------
 # energies and cuts of given (seeded) spin vectors
 # ---------------------------------------------------------------------------
