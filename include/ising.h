@@ -147,8 +147,10 @@ ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double e
 /*
  * Validate J and h (symmetry, zero diagonal, index ranges, finite values;
  * skipped with ISING_FLAG_SKIP_VALIDATION) and copy them to device memory
- * owned by a new handle. Dense +-1 couplings are held as exact FP8 E4M3 for
- * the tensor-core path. On failure *out is NULL.
+ * owned by a new handle. Dense couplings must be integers with |J| <= 256
+ * (ISING_ERR_UNSUPPORTED otherwise); they are held in the tensor-core tile
+ * order, as packed 2-bit codes when every entry is -1, 0 or +1 and as BF16
+ * otherwise (both exact). On failure *out is NULL.
  */
 ISING_API ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out);
 
@@ -174,6 +176,32 @@ ISING_API void ising_destroy(ising_handle_t h);
 ISING_API ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                              const double *alpha, int32_t alpha_len, const double *beta,
                              int32_t iters, double *H_trace, void *stream);
+
+/*
+ * ADOCH, Algorithm 2: DOCH with an extrapolated point that is kept only when
+ * it passes a non-monotone test on H (Eq. Hamilton):
+ *   t_0 = 1, t_(k+1) = (1 + sqrt(1 + 4 t_k^2)) / 2,
+ *   y^k = x^k + ((t_k - 1) / t_(k+1)) (x^k - x^(k-1)),  y^0 = x^0,
+ *   v^k = y^k if H(y^k) <= max(H(x^max(0,k-q)), ..., H(x^k)), else x^k,
+ *   x^(k+1) = T(v^k)  (Eq. FPE).
+ * Each step costs one coupling product (J y^k = (1 + c_k) J x^k - c_k J x^(k-1)),
+ * FP64 reductions of H(x^k) and H(y^k) per (instance, replica), and the
+ * update; the acceptance test runs per (instance, replica) on the device.
+ *   x      [n][R] F32 or F64, x^(0) on entry, x^(iters) on return (in place).
+ *   alpha, beta  [max(1,n_instances)] host arrays (constant alpha; beta > 0).
+ *   q      window of the non-monotone test (q >= 0; q = 0 compares with
+ *          H(x^k) alone).
+ *   accepted  NULL, or [iters][max(1,n_instances)][R] int8 (host or device):
+ *          1 where v^k = y^k.
+ *   H_trace   NULL, or [iters + 1][max(1,n_instances)][R] FP64 (host or
+ *          device): H(x^(k)) for k = 0 .. iters.
+ * CSR and TORUS2D couplings; ISING_ERR_UNSUPPORTED for DENSE. Device
+ * scratch: four iterate-sized buffers plus O(R) reduction space, owned by
+ * the handle.
+ */
+ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int32_t R,
+                                   const double *alpha, const double *beta, int32_t iters, int32_t q,
+                                   int8_t *accepted, double *H_trace, void *stream);
 
 /*
  * Sign rounding (Algorithm 1, step 5: s = sign(x^(N)), sign(0) = +1) and the

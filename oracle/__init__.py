@@ -316,7 +316,8 @@ def alpha_beta(J, eta: float = 1.0, method: str = "auto"):
 # ADOCH, Algorithm 2
 # ---------------------------------------------------------------------------
 
-def adoch(p: Problem, x0, alpha: float, beta: float, iters: int, q: int):
+def adoch(p: Problem, x0, alpha: float, beta: float, iters: int, q: int, decisions=None,
+          margins: bool = False):
     """Algorithm 2 (ADOCH) per replica: returns x^(N) ([n][R]) and the
     per-iteration acceptance flags [N][R] (1 where the extrapolated point was used).
 
@@ -324,11 +325,18 @@ def adoch(p: Problem, x0, alpha: float, beta: float, iters: int, q: int):
     y^k = x^k + ((t_k - 1)/t_(k+1)) (x^k - x^(k-1)), y^0 = x^0;
     v^k = y^k if H(y^k) <= max(H(x^(max(0,k-q))), ..., H(x^k)) else x^k;
     x^(k+1) = T(v^k).
+
+    decisions: optional [N][R] flags that replace the test (v^k = y^k where 1),
+    to follow a trajectory whose near-tied decisions were taken elsewhere.
+    margins: also return the signed margin (window max - H(y^k)) / |H(x^k)| of
+    the test per step and replica (>= 0 where it accepts; inf at k = 0, where
+    y^0 = x^0 and the test accepts exactly).
     """
     x = _state(x0, p.n)
     R = x.shape[1]
     out = np.empty_like(x)
     acc = np.zeros((iters, R), dtype=np.int8)
+    marg = np.full((iters, R), np.inf)
     for r in range(R):
         xk = x[:, r:r + 1].copy()
         xprev = xk.copy()
@@ -341,7 +349,11 @@ def adoch(p: Problem, x0, alpha: float, beta: float, iters: int, q: int):
             else:
                 y = xk.copy()
             window = hist[max(0, k - q):k + 1]
-            if hamiltonian(p, y, alpha, beta)[0] <= max(window):
+            hy = hamiltonian(p, y, alpha, beta)[0]
+            if k >= 1:
+                marg[k, r] = (max(window) - hy) / abs(hist[-1])
+            take = hy <= max(window) if decisions is None else bool(decisions[k][r])
+            if take:
                 v = y
                 acc[k, r] = 1
             else:
@@ -351,4 +363,6 @@ def adoch(p: Problem, x0, alpha: float, beta: float, iters: int, q: int):
             hist.append(hamiltonian(p, xk, alpha, beta)[0])
             t = t_next
         out[:, r] = xk[:, 0]
+    if margins:
+        return out, acc, marg
     return out, acc

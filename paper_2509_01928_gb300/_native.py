@@ -69,6 +69,8 @@ def load():
     lib.ising_destroy.restype = None
     lib.ising_iterate.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32, _vp,
                                   ctypes.c_int32, _vp, _vp]
+    lib.ising_iterate_adoch.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32,
+                                        ctypes.c_int32, _vp, _vp, _vp]
     lib.ising_energy.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     lib.ising_backward.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
@@ -83,7 +85,7 @@ def load():
     lib.ising_status_string.restype = ctypes.c_char_p
     lib.ising_last_error.argtypes = []
     lib.ising_last_error.restype = ctypes.c_char_p
-    for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_energy",
+    for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_iterate_adoch", "ising_energy",
                  "ising_backward", "ising_synchronize", "ising_get_size"):
         getattr(lib, name).restype = st
     _lib = lib
@@ -241,6 +243,20 @@ def ising_iterate(handle: int, x, alpha, beta, iters: int, H_trace=None, stream=
     _check(load().ising_iterate(handle, _ptr(x), _dtype_code(x), R, a.ctypes.data, alpha_len,
                                 b.ctypes.data, int(iters), _ptr(H_trace), _stream(stream, x)),
            "ising_iterate")
+    return x
+
+
+def ising_iterate_adoch(handle: int, x, alpha, beta, iters: int, q: int, accepted=None, H_trace=None,
+                        stream=None):
+    """In-place ADOCH iterations (Algorithm 2) on x ([n][R] or [n]); alpha [B] and beta [B] host values;
+    optional accepted [iters][B R] int8 and H_trace [iters + 1][B R] FP64 outputs."""
+    R = 1 if x.ndim == 1 else int(x.shape[1])
+    a = _f64(alpha)
+    b = _f64(beta)
+    _check(load().ising_iterate_adoch(handle, _ptr(x), _dtype_code(x), R, a.ctypes.data, b.ctypes.data,
+                                      int(iters), int(q), _ptr(accepted), _ptr(H_trace),
+                                      _stream(stream, x, accepted, H_trace)),
+           "ising_iterate_adoch")
     return x
 
 

@@ -910,6 +910,70 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
     return finish(c, st, must_sync);
 }
 
+ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
+                                   const double *beta, int32_t iters, int32_t q, int8_t *accepted,
+                                   double *H_trace, void *stream) {
+    g_err.clear();
+    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (R < 1 || R > 65535 || iters < 0 || q < 0)
+        return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, iters >= 0 and q >= 0");
+    if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
+    ising_context *c = h;
+    if (c->format != ISING_FMT_CSR && c->format != ISING_FMT_TORUS2D)
+        return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR or TORUS2D couplings");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t count = c->n * R;
+    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+    ParamTabs p;
+    DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
+    const bool x_dev = is_device_ptr(x);
+    void *xd = x;
+    if (!x_dev) {
+        DOCH_CHECK(c->stage_x.ensure(xbytes));
+        xd = c->stage_x.ptr;
+        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
+    }
+    const int pairs = c->n_inst * R;
+    const size_t ab = static_cast<size_t>(pairs) * iters;
+    const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
+    int8_t *acc_dev = nullptr;
+    double *H_dev = nullptr;
+    const bool acc_on_dev = accepted && is_device_ptr(accepted);
+    const bool H_on_dev = H_trace && is_device_ptr(H_trace);
+    if (accepted) {
+        if (acc_on_dev) {
+            acc_dev = accepted;
+        } else {
+            DOCH_CHECK(c->stage_out.ensure(ab + 1));
+            acc_dev = c->stage_out.as<int8_t>();
+        }
+    }
+    if (H_trace) {
+        if (H_on_dev) {
+            H_dev = H_trace;
+        } else {
+            DOCH_CHECK(c->work.ensure(hb));
+            H_dev = c->work.as<double>();
+        }
+    }
+    if (iters > 0) DOCH_CHECK(adoch_iterate(c, xd, xtype, R, p, iters, q, acc_dev, H_dev, st));
+    if (H_dev) DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, H_dev + static_cast<size_t>(iters) * pairs, st));
+    bool must_sync = false;
+    if (!x_dev) {
+        DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+        must_sync = true;
+    }
+    if (accepted && !acc_on_dev && ab > 0) {
+        DOCH_CUDA(cudaMemcpyAsync(accepted, acc_dev, ab, cudaMemcpyDeviceToHost, st));
+        must_sync = true;
+    }
+    if (H_trace && !H_on_dev) {
+        DOCH_CUDA(cudaMemcpyAsync(H_trace, H_dev, hb, cudaMemcpyDeviceToHost, st));
+        must_sync = true;
+    }
+    return finish(c, st, must_sync);
+}
+
 ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int32_t R, int64_t *E_int,
                             int64_t *cut_int, double *E_f64, double *cut_f64, int32_t *best, int8_t *spins,
                             void *stream) {

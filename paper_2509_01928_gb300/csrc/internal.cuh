@@ -188,6 +188,13 @@ ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, in
 
 // Batched persistent kernel (k_batched.cu): FP32 iterates, ping-pong xa <-> xb;
 // after `iters` steps the result is in xa (iters even) or xb (odd).
+// ADOCH (Algorithm 2) for CSR or TORUS2D couplings, F32 or F64 iterates, all
+// instances: `iters` steps with history window q; per step and (instance,
+// replica) pair the acceptance flag (acc_dev[k][pair], may be NULL) and H(x^k)
+// (H_dev[k][pair], may be NULL) are written; x is updated in place.
+ising_status_t adoch_iterate(ising_context *c, void *x, int xtype, int R, const ParamTabs &p, int iters, int q,
+                             int8_t *acc_dev, double *H_dev, cudaStream_t st);
+
 // Batched instances with each (instance, replica group) resident in shared
 // memory for all steps (k_batched.cu); ISING_ERR_UNSUPPORTED when an instance
 // does not fit or x is not 16-byte aligned. Updates x in place.

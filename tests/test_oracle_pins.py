@@ -450,3 +450,25 @@ def test_adoch_two_spin():
     x0 = np.array([[0.7, -0.2], [0.1, 0.5]])
     x, _ = O.adoch(O.Problem(J), x0, g["alpha"][0], g["beta"][0], 60, q=5)
     np.testing.assert_allclose(x, [[1.0, -1.0], [-1.0, 1.0]], atol=1e-9)
+
+
+def test_adoch_decision_replay():
+    """Replaying ADOCH's own decisions reproduces it bit for bit; rejecting every
+    extrapolation (v^k = x^k throughout) reduces Algorithm 2 to Algorithm 1 (x^(k+1)
+    = T(x^k)); the signed margins are infinite at k = 0 (y^0 = x^0) and their sign
+    is the test's decision."""
+    J = _sk(40, seed=34)
+    p = O.Problem(J)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    x0 = I.x0_uniform(40, 3, seed=35, dtype=np.float64)
+    iters, q = 25, 1
+    x, acc, m = O.adoch(p, x0, alpha, beta, iters, q, margins=True)
+    xr, accr = O.adoch(p, x0, alpha, beta, iters, q, decisions=acc)
+    np.testing.assert_array_equal(xr, x)
+    np.testing.assert_array_equal(accr, acc)
+    assert 0 < acc[1:].mean() < 1          # both branches occur
+    x0s, acc0 = O.adoch(p, x0, alpha, beta, iters, q, decisions=np.zeros((iters, 3), np.int8))
+    np.testing.assert_allclose(x0s, O.doch(p, x0, alpha, beta, iters), rtol=0, atol=1e-15)
+    assert not acc0.any()
+    assert np.isinf(m[0]).all() and np.isfinite(m[1:]).all()
+    np.testing.assert_array_equal(acc[1:], (m[1:] >= 0).astype(np.int8))
