@@ -555,7 +555,87 @@ class Er800:
         self.N.ising_destroy(self.h)
 
 
-WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800}
+class Adoch:
+    """ADOCH (Algorithm 2) on the 10^4 x 10^4 lattice, FP32, R = 1, q = 5, 100 steps per timed step."""
+
+    dominant = "adoch step (adoch_pass + adoch_decide + adoch_update)"
+    dtype = "f32"
+
+    def __init__(self, args, rank, N, I, torch):
+        self.L, self.iters, self.R, self.q = args.size, args.adoch_iters, 1, 5
+        self.n = self.L * self.L
+        t = I.torus_pm1(self.L, self.L, seed=SEED + 1000 * rank)
+        self.x0 = I.x0_uniform(self.n, 1, seed=SEED + 1000 * rank)
+        prob = N.Problem(t)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.acc = torch.zeros((self.iters, 1), dtype=torch.int8, device="cuda")
+        self.E = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters  # one ADOCH step = pass + decide + update
+        self.launches = 3 * self.iters + 2 + 2
+        self.config = {"workload": f"ADOCH (Algorithm 2) on the torus2d {self.L}x{self.L} +-1 int8 lattice, FP32, "
+                                   f"R=1, q={self.q}, {self.iters} steps + sign + int64 energy",
+                       "n": self.n, "replicas": 1, "iters": self.iters, "q": self.q,
+                       "l2": "inputs larger than L2 (2 GB live per step); no flush",
+                       "alpha_beta": "Wigner estimate, eta = 1, beta of Eq. alphabeta"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate_adoch(self.h, self.x, self.alpha, self.beta, self.iters, self.q, accepted=self.acc,
+                              stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, stream=sid)
+
+    def roofline(self, per_launch_s):
+        peak, kind = measured_peaks()
+        # per step and site: pass reads x^k, x^(k-1), u^(k-1) and the couplings, writes u^k
+        # (4 + 4 + 4 + 2 + 4 B); update reads x^k, x^(k-1), u^k, u^(k-1), writes x^(k+1) (20 B)
+        alg = 38 * self.n
+        ach = alg / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": kind,
+                "algorithmic_bytes_per_launch": alg, "launch": "one ADOCH step (3 kernels)"}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        Eh = np.zeros(1, np.int64)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate_adoch(self.h, xh, self.alpha, self.beta, self.iters, self.q, stream=sid)
+            N.ising_energy(self.h, xh, E_int=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        return dt, 2 * self.n * 4, self.n * 4 + 8, "ising_iterate_adoch + ising_energy on pinned host arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        lr = lc = 1024
+        iters = 60
+        t = I.torus_pm1(lr, lc, seed=SEED)
+        x0 = I.x0_uniform(t.n, 1, seed=SEED)
+        P = O.Problem(t)
+        a, b = O.alpha_beta(t, eta=1.0, method="wigner")
+        t0 = time.perf_counter()
+        O.adoch(P, x0, a, b, iters, self.q)
+        dt = time.perf_counter() - t0
+        return {"value": t.n * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"ADOCH on a torus {lr}x{lc} int8 +-1, {iters} FP64 steps, q = {self.q}"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800,
+             "adoch": Adoch}
 
 
 def run_ours(args):
@@ -670,11 +750,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="torus", choices=sorted(WORKLOADS),
                     help="torus (default: 10^4 x 10^4 lattice), dense (16384 x 256 on tcgen05), "
-                         "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64)")
+                         "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64), "
+                         "adoch (Algorithm 2 on the 10^4 x 10^4 lattice)")
     ap.add_argument("--dense-n", type=int, default=16384)
     ap.add_argument("--dense-iters", type=int, default=1000)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=2000)
+    ap.add_argument("--adoch-iters", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -9,12 +9,15 @@
 // J y^k = (1 + c_k) u^k - c_k u^{k-1}, and J v^k is u^k or J y^k. Each step is
 //  (1) pass: u^k and, per (instance, replica, chunk) block, FP64 partial sums
 //      of the terms of H(x^k) and H(y^k) in a fixed order;
-//  (2) decide: one thread per (instance, replica) adds the chunk partials in
-//      order, forms H(x^k) and H(y^k), keeps the last q+1 values of H(x) and
-//      sets the acceptance flag;
+//  (2) decide: one block per (instance, replica) adds the chunk partials in a
+//      fixed order, forms H(x^k) and H(y^k), keeps the last q+1 values of H(x)
+//      and sets the acceptance flag;
 //  (3) update: x^{k+1} = T(v^k) element-wise.
 // The coupling product and the update run in the iterate's precision (as the
-// DOCH step kernels); H is reduced in FP64.
+// DOCH step kernels); H is reduced in FP64 across threads and blocks. With
+// FP32 iterates each thread first sums its sites' terms in FP32 with Kahan
+// compensation (FP64 arithmetic is a small fraction of the FP32 rate here),
+// with FP64 iterates in FP64.
 #include <cmath>
 #include <utility>
 
@@ -45,7 +48,8 @@ struct CsrProduct {
     const int64_t *row_ptr;
     const int32_t *col;
     const VT *val;
-    __device__ XT operator()(const XT *x, int64_t i, int r, int R) const {
+    static constexpr bool kGrid = false;
+    __device__ XT operator()(const XT *x, int64_t i, int64_t, int64_t, int r, int R) const {
         XT acc = XT(0);
         const int64_t e1 = row_ptr[i + 1];
         for (int64_t e = row_ptr[i]; e < e1; ++e)
@@ -58,8 +62,8 @@ template <typename XT>
 struct TorusProduct {
     const int8_t *right, *down;
     int64_t Lr, Lc;
-    __device__ XT operator()(const XT *x, int64_t i, int r, int R) const {
-        const int64_t rr = i / Lc, cc = i - rr * Lc;
+    static constexpr bool kGrid = true;  // wants the (row, column) of site i
+    __device__ XT operator()(const XT *x, int64_t i, int64_t rr, int64_t cc, int r, int R) const {
         const int64_t s_l = rr * Lc + (cc == 0 ? Lc - 1 : cc - 1);
         const int64_t s_r = rr * Lc + (cc + 1 == Lc ? 0 : cc + 1);
         const int64_t s_u = (rr == 0 ? Lr - 1 : rr - 1) * Lc + cc;
@@ -87,33 +91,58 @@ adoch_pass(Fn fn, const XT *__restrict__ x1, const XT *__restrict__ x0, const XT
     const int64_t hi = inst_off ? inst_off[b + 1] : n;
     const int64_t len = hi - lo;
     const int64_t s0 = lo + len * ch / chunks, s1 = lo + len * (ch + 1) / chunks;
-    double acc[kTerms];
+    // per-thread sums: FP32 with Kahan compensation for FP32 iterates, FP64 otherwise
+    using Acc = XT;
+    Acc acc[kTerms], cmp[kTerms];
 #pragma unroll
-    for (int k = 0; k < kTerms; ++k) acc[k] = 0.0;
+    for (int k = 0; k < kTerms; ++k) acc[k] = cmp[k] = Acc(0);
+    auto add = [&](int k, Acc v) {
+        if constexpr (sizeof(XT) == 4) {
+            const Acc y = v - cmp[k];
+            const Acc t = acc[k] + y;
+            cmp[k] = (t - acc[k]) - y;
+            acc[k] = t;
+        } else {
+            acc[k] += v;
+        }
+    };
+    // (row, column) of the site, advanced without division (lattice only)
+    int64_t rr = 0, cc = 0, Lc = 1;
+    if constexpr (Fn::kGrid) {
+        Lc = fn.Lc;
+        rr = (s0 + threadIdx.x) / Lc;
+        cc = (s0 + threadIdx.x) - rr * Lc;
+    }
     for (int64_t i = s0 + threadIdx.x; i < s1; i += kAThreads) {
         const int64_t at = i * R + r;
-        const XT u = fn(x1, i, r, R);
+        const XT u = fn(x1, i, rr, cc, r, R);
         u1[at] = u;
         const XT xv = x1[at];
         const XT y = xv + c * (xv - x0[at]);
         const XT jy = (XT(1) + c) * u - c * u0[at];
-        const double hv = h ? h[i] : 0.0;
-        const double xd = static_cast<double>(xv), yd = static_cast<double>(y);
-        const double x2 = xd * xd, y2 = yd * yd;
-        acc[0] += x2 * x2;
-        acc[1] += x2;
-        acc[2] += xd * static_cast<double>(u);
-        acc[3] += hv * xd;
-        acc[4] += y2 * y2;
-        acc[5] += y2;
-        acc[6] += yd * static_cast<double>(jy);
-        acc[7] += hv * yd;
+        const XT hv = h ? static_cast<XT>(h[i]) : XT(0);
+        const XT x2 = xv * xv, y2 = y * y;
+        add(0, x2 * x2);
+        add(1, x2);
+        add(2, xv * u);
+        add(3, hv * xv);
+        add(4, y2 * y2);
+        add(5, y2);
+        add(6, y * jy);
+        add(7, hv * y);
+        if constexpr (Fn::kGrid) {
+            cc += kAThreads;
+            while (cc >= Lc) {
+                cc -= Lc;
+                ++rr;
+            }
+        }
     }
     __shared__ double red[kAThreads / 32][kTerms];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < kTerms; ++k) {
-        const double v = warp_sum(acc[k]);
+        const double v = warp_sum(static_cast<double>(acc[k]) - static_cast<double>(cmp[k]));
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
@@ -124,23 +153,36 @@ adoch_pass(Fn fn, const XT *__restrict__ x1, const XT *__restrict__ x0, const XT
     }
 }
 
-// (2) one thread per (instance, replica) pair t = b R + r
-__global__ void adoch_decide(const double *__restrict__ partials, int n_inst, int R, int chunks,
-                             const double *__restrict__ alpha_tab, const double *__restrict__ beta_tab, int k, int q,
-                             double *__restrict__ hist, int *__restrict__ dec, int8_t *__restrict__ acc_out,
-                             double *__restrict__ H_out) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_inst * R) return;
+// (2) one block per (instance, replica) pair t = b R + r: the chunk partials
+// are added by the block's threads in a fixed strided order and a fixed tree
+constexpr int kDThreads = 128;
+__global__ void __launch_bounds__(kDThreads)
+adoch_decide(const double *__restrict__ partials, int n_inst, int R, int chunks,
+             const double *__restrict__ alpha_tab, const double *__restrict__ beta_tab, int k, int q,
+             double *__restrict__ hist, int *__restrict__ dec, int8_t *__restrict__ acc_out,
+             double *__restrict__ H_out) {
+    const int t = blockIdx.x;
     const int b = t / R;
+    __shared__ double red[kDThreads][kTerms];
     double s[kTerms];
 #pragma unroll
     for (int j = 0; j < kTerms; ++j) s[j] = 0.0;
-    for (int ch = 0; ch < chunks; ++ch)
+    for (int ch = threadIdx.x; ch < chunks; ch += kDThreads)
 #pragma unroll
         for (int j = 0; j < kTerms; ++j) s[j] += partials[(static_cast<int64_t>(t) * chunks + ch) * kTerms + j];
+#pragma unroll
+    for (int j = 0; j < kTerms; ++j) red[threadIdx.x][j] = s[j];
+    __syncthreads();
+    for (int w = kDThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int j = 0; j < kTerms; ++j) red[threadIdx.x][j] += red[threadIdx.x + w][j];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     const double a = alpha_tab[b], be = beta_tab[b];
-    const double Hx = be / 4.0 * s[0] - a / 2.0 * s[1] - 0.5 * s[2] - s[3];
-    const double Hy = be / 4.0 * s[4] - a / 2.0 * s[5] - 0.5 * s[6] - s[7];
+    const double Hx = be / 4.0 * red[0][0] - a / 2.0 * red[0][1] - 0.5 * red[0][2] - red[0][3];
+    const double Hy = be / 4.0 * red[0][4] - a / 2.0 * red[0][5] - 0.5 * red[0][6] - red[0][7];
     double *ht = hist + static_cast<int64_t>(t) * (q + 1);
     ht[k % (q + 1)] = Hx;
     double m = Hx;
@@ -226,8 +268,8 @@ ising_status_t adoch_run(ising_context *c, const Fn &fn, XT *x, int R, const Par
         const XT ck = static_cast<XT>(k >= 1 ? (t - 1.0) / t_next : 0.0);
         adoch_pass<XT, Fn><<<grid, kAThreads, 0, st>>>(fn, x1, x0, u0, u1, h_d, off, c->n, R, chunks, ck, part);
         DOCH_CUDA(cudaGetLastError());
-        adoch_decide<<<(pairs + 127) / 128, 128, 0, st>>>(part, c->n_inst, R, chunks, p.alpha_d, p.beta_d, k, q,
-                                                          hist, dec, acc_dev, H_dev);
+        adoch_decide<<<pairs, kDThreads, 0, st>>>(part, c->n_inst, R, chunks, p.alpha_d, p.beta_d, k, q, hist,
+                                                  dec, acc_dev, H_dev);
         DOCH_CUDA(cudaGetLastError());
         adoch_update<XT><<<grid, kAThreads, 0, st>>>(x1, x0, u1, u0, x2, h_x, off, c->n, R, chunks, ck, alpha,
                                                      beta, dec);
