@@ -204,6 +204,24 @@ ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t 
                                    int8_t *accepted, double *H_trace, void *stream);
 
 /*
+ * DOCH (Algorithm 1) with the stopping rule of Remark S2, per (instance,
+ * replica) pair: after each step, r^(k) = ||x^(k+1) - x^(k)||_2 / ||x^(k)||_2
+ * (FP64 reduction on the device); the pair stops at the first k with
+ * r^(k) < eps and keeps x^(k+1). Pairs that never meet the rule run
+ * max_iters steps.
+ *   x      [n][R] F32 or F64 (in place): each pair's last iterate on return.
+ *   alpha, beta  [max(1,n_instances)] host arrays (constant alpha).
+ *   eps    >= 0 (0 never stops).
+ *   steps_out  NULL, or [max(1,n_instances)][R] int32 (host or device): the
+ *          steps each pair took.
+ * The host checks every 8 steps whether any pair still runs and ends the
+ * loop when none does. CSR and TORUS2D; ISING_ERR_UNSUPPORTED for DENSE.
+ */
+ISING_API ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int32_t R,
+                                   const double *alpha, const double *beta, int32_t max_iters, double eps,
+                                   int32_t *steps_out, void *stream);
+
+/*
  * Sign rounding (Algorithm 1, step 5: s = sign(x^(N)), sign(0) = +1) and the
  * Ising energy E_r = -1/2 s_r^T J s_r - h^T s_r (Eq. IsingModel) with the cut
  * value cut_r = 1/4 sum_ij (1 - s_i s_j) W_ij for W = -2J (Supplementary

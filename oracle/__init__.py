@@ -207,6 +207,29 @@ def doch(p: Problem, x0, alpha, beta: float, iters: int, trace: bool = False):
     return (x, H) if trace else x
 
 
+def doch_until(p: Problem, x0, alpha: float, beta: float, max_iters: int, eps: float):
+    """Algorithm 1 with the stopping rule of Remark S2, per replica: after each
+    step, r^(k) = ||x^(k+1) - x^(k)||_2 / ||x^(k)||_2; the replica stops at the
+    first k with r^(k) < eps, keeping x^(k+1). Returns x ([n][R], each replica's
+    last iterate), the steps taken per replica ([R], <= max_iters) and the
+    trace r ([max_iters][R], NaN after a replica stopped)."""
+    x = _state(x0, p.n)
+    R = x.shape[1]
+    steps = np.full(R, max_iters, dtype=np.int32)
+    rtr = np.full((max_iters, R), np.nan)
+    for r in range(R):
+        xk = x[:, r:r + 1].copy()
+        for k in range(max_iters):
+            xn = doch(p, xk, alpha, beta, 1)
+            rtr[k, r] = np.linalg.norm(xn - xk) / np.linalg.norm(xk)
+            xk = xn
+            if rtr[k, r] < eps:
+                steps[r] = k + 1
+                break
+        x[:, r] = xk[:, 0]
+    return x, steps, rtr
+
+
 def sign(x) -> np.ndarray:
     """s = sign(x) with sign(0) = +1, int8."""
     x = np.ascontiguousarray(x, dtype=np.float64)

@@ -71,6 +71,8 @@ def load():
                                   ctypes.c_int32, _vp, _vp]
     lib.ising_iterate_adoch.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32,
                                         ctypes.c_int32, _vp, _vp, _vp]
+    lib.ising_iterate_until.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32,
+                                        ctypes.c_double, _vp, _vp]
     lib.ising_energy.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     lib.ising_backward.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
@@ -85,7 +87,8 @@ def load():
     lib.ising_status_string.restype = ctypes.c_char_p
     lib.ising_last_error.argtypes = []
     lib.ising_last_error.restype = ctypes.c_char_p
-    for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_iterate_adoch", "ising_energy",
+    for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_iterate_adoch", "ising_iterate_until",
+                 "ising_energy",
                  "ising_backward", "ising_synchronize", "ising_get_size"):
         getattr(lib, name).restype = st
     _lib = lib
@@ -257,6 +260,18 @@ def ising_iterate_adoch(handle: int, x, alpha, beta, iters: int, q: int, accepte
                                       int(iters), int(q), _ptr(accepted), _ptr(H_trace),
                                       _stream(stream, x, accepted, H_trace)),
            "ising_iterate_adoch")
+    return x
+
+
+def ising_iterate_until(handle: int, x, alpha, beta, max_iters: int, eps: float, steps=None, stream=None):
+    """DOCH with the stopping rule of Remark S2 per (instance, replica), in place on x;
+    alpha [B] and beta [B] host values; optional steps [B R] int32 output."""
+    R = 1 if x.ndim == 1 else int(x.shape[1])
+    a = _f64(alpha)
+    b = _f64(beta)
+    _check(load().ising_iterate_until(handle, _ptr(x), _dtype_code(x), R, a.ctypes.data, b.ctypes.data,
+                                      int(max_iters), float(eps), _ptr(steps), _stream(stream, x, steps)),
+           "ising_iterate_until")
     return x
 
 

@@ -383,6 +383,7 @@ void destroy_ctx(ising_context *c) {
     cudaFree(c->h_i64);
     cudaFree(c->err_word);
     if (c->err_host) cudaFreeHost(c->err_host);
+    if (c->count_host) cudaFreeHost(c->count_host);
     cudaFree(c->batch_order);
     cudaFree(c->ell_col);
     cudaFree(c->ell_val);
@@ -970,6 +971,86 @@ ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int
     if (H_trace && !H_on_dev) {
         DOCH_CUDA(cudaMemcpyAsync(H_trace, H_dev, hb, cudaMemcpyDeviceToHost, st));
         must_sync = true;
+    }
+    return finish(c, st, must_sync);
+}
+
+ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
+                                   const double *beta, int32_t max_iters, double eps, int32_t *steps_out,
+                                   void *stream) {
+    g_err.clear();
+    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (R < 1 || R > 65535 || max_iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, max_iters >= 0");
+    if (!std::isfinite(eps) || eps < 0.0) return fail(ISING_ERR_INVALID_ARG, "eps must be finite and >= 0");
+    if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
+    ising_context *c = h;
+    if (c->format == ISING_FMT_DENSE) return fail(ISING_ERR_UNSUPPORTED, "the stopping rule runs on CSR or TORUS2D");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t count = c->n * R;
+    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+    const int pairs = c->n_inst * R;
+    std::vector<double> alpha_h(c->n_inst), beta_h(c->n_inst);
+    {
+        std::vector<unsigned char> tmp;
+        DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
+        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
+        DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
+        std::memcpy(beta_h.data(), tmp.data(), tmp.size());
+    }
+    ParamTabs p;
+    DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
+    const bool x_dev = is_device_ptr(x);
+    void *xd = x;
+    if (!x_dev) {
+        DOCH_CHECK(c->stage_x.ensure(xbytes));
+        xd = c->stage_x.ptr;
+        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
+    }
+    // work: result | partials | running | steps | stopped_now | n_running (256-byte aligned)
+    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t o1 = al(xbytes), o2 = o1 + al(stop_partials_bytes(c, R)), o3 = o2 + al(sizeof(int) * pairs),
+                 o4 = o3 + al(sizeof(int32_t) * pairs), o5 = o4 + al(sizeof(int) * pairs), tot = o5 + 256;
+    DOCH_CHECK(c->work.ensure(tot));
+    unsigned char *wb = c->work.as<unsigned char>();
+    void *res = wb;
+    StopState s;
+    s.partials = reinterpret_cast<double *>(wb + o1);
+    s.running = reinterpret_cast<int *>(wb + o2);
+    s.steps = reinterpret_cast<int32_t *>(wb + o3);
+    s.stopped_now = reinterpret_cast<int *>(wb + o4);
+    s.n_running = reinterpret_cast<int *>(wb + o5);
+    {
+        std::vector<int> ones(pairs, 1), st0(pairs, max_iters);
+        DOCH_CUDA(cudaMemcpyAsync(s.running, ones.data(), sizeof(int) * pairs, cudaMemcpyHostToDevice, st));
+        DOCH_CUDA(cudaMemcpyAsync(s.steps, st0.data(), sizeof(int32_t) * pairs, cudaMemcpyHostToDevice, st));
+        DOCH_CUDA(cudaMemcpyAsync(s.n_running, &pairs, sizeof(int), cudaMemcpyHostToDevice, st));
+        DOCH_CUDA(cudaMemsetAsync(s.stopped_now, 0, sizeof(int) * pairs, st));
+        DOCH_CUDA(cudaStreamSynchronize(st));  // the sources are pageable
+    }
+    if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
+    DOCH_CHECK(c->ping.ensure(xbytes));
+    void *cur = xd, *nxt = c->ping.ptr;
+    constexpr int kPoll = 8;  // steps between host checks of the running-pair count
+    for (int k = 0; k < max_iters; ++k) {
+        DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+        DOCH_CHECK(stop_step(c, cur, nxt, res, xtype, R, eps, k, s, st));
+        std::swap(cur, nxt);
+        if ((k + 1) % kPoll == 0 && k + 1 < max_iters) {
+            DOCH_CUDA(cudaMemcpyAsync(c->count_host, s.n_running, sizeof(int), cudaMemcpyDeviceToHost, st));
+            DOCH_CUDA(cudaStreamSynchronize(st));
+            if (*c->count_host == 0) break;
+        }
+    }
+    DOCH_CHECK(stop_finish(c, cur, res, xtype, R, s, st));
+    DOCH_CUDA(cudaMemcpyAsync(xd, res, xbytes, cudaMemcpyDeviceToDevice, st));
+    bool must_sync = false;
+    if (!x_dev) {
+        DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+        must_sync = true;
+    }
+    if (steps_out) {
+        DOCH_CUDA(cudaMemcpyAsync(steps_out, s.steps, sizeof(int32_t) * pairs, cudaMemcpyDefault, st));
+        if (!is_device_ptr(steps_out)) must_sync = true;
     }
     return finish(c, st, must_sync);
 }

@@ -105,6 +105,7 @@ struct ising_context {
     doch::DevBuf work;      // misc. work space
     int *err_word = nullptr;  // device error word
     int *err_host = nullptr;  // pinned mirror
+    int *count_host = nullptr;  // pinned: running-pair count of the stopping rule
     // batched instances: longest-first queue order, queue counter, tuned shapes,
     // and the captured graph of the persistent launch with the key it was built for
     int32_t *batch_order = nullptr;
@@ -194,6 +195,23 @@ ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, in
 // (H_dev[k][pair], may be NULL) are written; x is updated in place.
 ising_status_t adoch_iterate(ising_context *c, void *x, int xtype, int R, const ParamTabs &p, int iters, int q,
                              int8_t *acc_dev, double *H_dev, cudaStream_t st);
+
+// Stopping rule of Remark S2 (k_stop.cu): device state per (instance,
+// replica) pair and the kernels run after each step x^(k) -> x^(k+1).
+struct StopState {
+    double *partials = nullptr;    // [pair][chunk][2]: sums of (x^(k+1) - x^(k))^2 and (x^(k))^2
+    int *running = nullptr;        // [pair] 1 while the pair runs
+    int32_t *steps = nullptr;      // [pair] steps taken (max_iters for a pair that never stops)
+    int *stopped_now = nullptr;    // [pair] 1 if the pair stopped at this step
+    int *n_running = nullptr;      // pairs still running
+};
+size_t stop_partials_bytes(const ising_context *c, int R);
+// r^(k) per pair; pairs stopping now record k + 1 and copy x^(k+1) (xn) into res
+ising_status_t stop_step(ising_context *c, const void *xc, const void *xn, void *res, int xtype, int R, double eps,
+                         int k, StopState &s, cudaStream_t st);
+// pairs still running take xc into res
+ising_status_t stop_finish(ising_context *c, const void *xc, void *res, int xtype, int R, StopState &s,
+                           cudaStream_t st);
 
 // Batched instances with each (instance, replica group) resident in shared
 // memory for all steps (k_batched.cu); ISING_ERR_UNSUPPORTED when an instance

@@ -472,3 +472,35 @@ def test_adoch_decision_replay():
     assert not acc0.any()
     assert np.isinf(m[0]).all() and np.isfinite(m[1:]).all()
     np.testing.assert_array_equal(acc[1:], (m[1:] >= 0).astype(np.int8))
+
+
+# ---------------------------------------------------------------------------
+# Stopping rule (Remark S2)
+# ---------------------------------------------------------------------------
+
+def test_stopping_rule_definition():
+    """doch_until stops each replica at the first step whose relative change
+    ||x^(k+1) - x^(k)|| / ||x^(k)|| (recomputed here from single DOCH steps) is
+    below eps, and returns that step's iterate; eps = 0 never stops (plain
+    Algorithm 1) and a huge eps stops after one step."""
+    J = _sk(50, seed=36)
+    p = O.Problem(J)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    x0 = I.x0_uniform(50, 4, seed=37, dtype=np.float64)
+    x, steps, rtr = O.doch_until(p, x0, alpha, beta, 200, 1e-6)
+    for r in range(4):
+        xk = x0[:, r:r + 1]
+        for k in range(steps[r]):
+            xn = O.doch(p, xk, alpha, beta, 1)
+            rk = np.linalg.norm(xn - xk) / np.linalg.norm(xk)
+            assert rk == rtr[k, r]
+            assert (rk < 1e-6) == (k == steps[r] - 1)
+            xk = xn
+        np.testing.assert_array_equal(x[:, r:r + 1], xk)
+    assert 1 < steps.min() and steps.max() < 200      # stops somewhere in between
+    x0s, s0, _ = O.doch_until(p, x0, alpha, beta, 30, 0.0)
+    np.testing.assert_array_equal(x0s, O.doch(p, x0, alpha, beta, 30))
+    assert (s0 == 30).all()
+    x1, s1, _ = O.doch_until(p, x0, alpha, beta, 30, 1e9)
+    np.testing.assert_array_equal(x1, O.doch(p, x0, alpha, beta, 1))
+    assert (s1 == 1).all()
