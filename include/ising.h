@@ -214,8 +214,12 @@ ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t 
  *   eps    >= 0 (0 never stops).
  *   steps_out  NULL, or [max(1,n_instances)][R] int32 (host or device): the
  *          steps each pair took.
- * The host checks every 8 steps whether any pair still runs and ends the
- * loop when none does. CSR and TORUS2D; ISING_ERR_UNSUPPORTED for DENSE.
+ * Batched FP32 instances that fit the shared-memory resident kernel apply
+ * the rule inside it (FP32 sums per thread and warp, FP64 across warps) and
+ * end each instance's replica group once all of its replicas stopped;
+ * otherwise the host checks every 8 steps whether any pair still runs and
+ * ends the loop when none does. CSR and TORUS2D; ISING_ERR_UNSUPPORTED for
+ * DENSE.
  */
 ISING_API ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                                    const double *alpha, const double *beta, int32_t max_iters, double eps,

@@ -1027,22 +1027,31 @@ ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int
         DOCH_CUDA(cudaMemsetAsync(s.stopped_now, 0, sizeof(int) * pairs, st));
         DOCH_CUDA(cudaStreamSynchronize(st));  // the sources are pageable
     }
-    if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
-    DOCH_CHECK(c->ping.ensure(xbytes));
-    void *cur = xd, *nxt = c->ping.ptr;
-    constexpr int kPoll = 8;  // steps between host checks of the running-pair count
-    for (int k = 0; k < max_iters; ++k) {
-        DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
-        DOCH_CHECK(stop_step(c, cur, nxt, res, xtype, R, eps, k, s, st));
-        std::swap(cur, nxt);
-        if ((k + 1) % kPoll == 0 && k + 1 < max_iters) {
-            DOCH_CUDA(cudaMemcpyAsync(c->count_host, s.n_running, sizeof(int), cudaMemcpyDeviceToHost, st));
-            DOCH_CUDA(cudaStreamSynchronize(st));
-            if (*c->count_host == 0) break;
+    // batched FP32 instances: the rule runs inside the shared-memory resident kernel, which
+    // ends each (instance, replica group) as soon as all of its replicas stopped
+    ising_status_t rs = ISING_ERR_UNSUPPORTED;
+    if (c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && max_iters > 0)
+        rs = batched_resident_launch(c, static_cast<float *>(xd), R, p, max_iters, st, static_cast<float>(eps),
+                                     s.steps);
+    if (rs != ISING_OK && rs != ISING_ERR_UNSUPPORTED) return rs;
+    if (rs == ISING_ERR_UNSUPPORTED) {
+        if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
+        DOCH_CHECK(c->ping.ensure(xbytes));
+        void *cur = xd, *nxt = c->ping.ptr;
+        constexpr int kPoll = 8;  // steps between host checks of the running-pair count
+        for (int k = 0; k < max_iters; ++k) {
+            DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+            DOCH_CHECK(stop_step(c, cur, nxt, res, xtype, R, eps, k, s, st));
+            std::swap(cur, nxt);
+            if ((k + 1) % kPoll == 0 && k + 1 < max_iters) {
+                DOCH_CUDA(cudaMemcpyAsync(c->count_host, s.n_running, sizeof(int), cudaMemcpyDeviceToHost, st));
+                DOCH_CUDA(cudaStreamSynchronize(st));
+                if (*c->count_host == 0) break;
+            }
         }
+        DOCH_CHECK(stop_finish(c, cur, res, xtype, R, s, st));
+        DOCH_CUDA(cudaMemcpyAsync(xd, res, xbytes, cudaMemcpyDeviceToDevice, st));
     }
-    DOCH_CHECK(stop_finish(c, cur, res, xtype, R, s, st));
-    DOCH_CUDA(cudaMemcpyAsync(xd, res, xbytes, cudaMemcpyDeviceToDevice, st));
     bool must_sync = false;
     if (!x_dev) {
         DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));

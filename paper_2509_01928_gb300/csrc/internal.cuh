@@ -215,9 +215,11 @@ ising_status_t stop_finish(ising_context *c, const void *xc, void *res, int xtyp
 
 // Batched instances with each (instance, replica group) resident in shared
 // memory for all steps (k_batched.cu); ISING_ERR_UNSUPPORTED when an instance
-// does not fit or x is not 16-byte aligned. Updates x in place.
+// does not fit or x is not 16-byte aligned. Updates x in place. eps > 0
+// applies the stopping rule of Remark S2 per (instance, replica) inside the
+// kernel (steps: [pair] steps taken, may be NULL).
 ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
-                                       cudaStream_t st);
+                                       cudaStream_t st, float eps = 0.f, int32_t *steps = nullptr);
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
                               const ParamTabs &p, int iters, cudaStream_t st);
 

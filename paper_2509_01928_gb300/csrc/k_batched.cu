@@ -192,21 +192,50 @@ __device__ __forceinline__ void st_vec(float *p, const float (&v)[G]) {
     }
 }
 
-template <int G>
+// Stopping rule of Remark S2 inside the resident kernel (eps > 0): block-wide
+// sums of (x^(k+1) - x^(k))^2 and (x^(k))^2 per replica of the item (FP32 per
+// thread and warp, FP64 across warps); a replica with r^(k) < eps is frozen
+// (its later updates keep x) and its step count written; the item ends when
+// all of its replicas are frozen.
+struct ResidentStop {
+    float eps;        // 0: no stopping rule
+    int32_t *steps;   // [pair] steps taken, or NULL
+    float (*red)[32]; // [warps][2 G] per-warp sums
+    int *frozen;      // [G]
+    int *all_frozen;
+};
+
+template <int G, bool STOP>
 __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int64_t lo, int nb, int g0, int D,
                                               const uint16_t *__restrict__ ecol, const float *__restrict__ eval,
                                               const float *__restrict__ h, const float *__restrict__ alpha_row,
-                                              int alpha_len, float zs, float xsc, int iters, float *s0, float *s1) {
+                                              int alpha_len, float zs, float xsc, int iters, float *s0, float *s1,
+                                              int pair0, const ResidentStop &stop) {
     const int T = blockDim.x;
+    constexpr bool stopping = STOP;
     for (int i = threadIdx.x; i < nb; i += T) {
         float v[G];
         ldg_vec<G>(x + (lo + i) * R + g0, v);
         st_vec<G>(s0 + i * G, v);
     }
+    if (STOP && threadIdx.x < G) {
+        stop.frozen[threadIdx.x] = 0;
+        if (stop.steps) stop.steps[pair0 + threadIdx.x] = iters;
+    }
+    if (STOP && threadIdx.x == 0) *stop.all_frozen = 0;
     __syncthreads();
     float *cur = s0, *nxt = s1;
     for (int k = 0; k < iters; ++k) {
         const float a = __ldg(alpha_row + (alpha_len == 1 ? 0 : k));
+        bool frz[STOP ? G : 1];
+        float dsum[STOP ? G : 1], ssum[STOP ? G : 1];
+        if constexpr (STOP) {
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                frz[q] = stop.frozen[q];
+                dsum[q] = ssum[q] = 0.f;
+            }
+        }
         for (int i = threadIdx.x; i < nb; i += T) {
             float acc[G];
 #pragma unroll
@@ -237,10 +266,54 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
             const float hv = h ? __ldg(h + lo + i) : 0.f;
 #pragma unroll
             for (int q = 0; q < G; ++q) out[q] = cbrt_pow2((acc[q] + a * xs[q] + hv) * zs) * xsc;
+            if constexpr (STOP) {
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    if (frz[q]) out[q] = xs[q];
+                    const float e = out[q] - xs[q];
+                    dsum[q] += e * e;
+                    ssum[q] += xs[q] * xs[q];
+                }
+            }
             st_vec<G>(nxt + i * G, out);
+        }
+        if constexpr (STOP) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+                    ssum[q] += __shfl_xor_sync(0xffffffffu, ssum[q], o);
+                }
+                if (lane == 0) {
+                    stop.red[warp][q] = dsum[q];
+                    stop.red[warp][G + q] = ssum[q];
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int all = 1;
+                for (int q = 0; q < G; ++q) {
+                    if (!stop.frozen[q]) {
+                        double dd = 0.0, ss = 0.0;
+                        for (int w = 0; w < T / 32; ++w) {
+                            dd += static_cast<double>(stop.red[w][q]);
+                            ss += static_cast<double>(stop.red[w][G + q]);
+                        }
+                        if (sqrt(dd) / sqrt(ss) < static_cast<double>(stop.eps)) {
+                            stop.frozen[q] = 1;
+                            if (stop.steps) stop.steps[pair0 + q] = k + 1;
+                        }
+                    }
+                    all &= stop.frozen[q];
+                }
+                *stop.all_frozen = all;
+            }
         }
         __syncthreads();
         float *t = cur; cur = nxt; nxt = t;
+        if (STOP && *stop.all_frozen) break;  // uniform: read after the barrier
     }
     for (int i = threadIdx.x; i < nb; i += T) {
         float v[G];
@@ -249,14 +322,19 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
     }
 }
 
+template <bool STOP>
 __global__ void __launch_bounds__(1024, 1)
 batched_resident(float *__restrict__ x, const uint16_t *__restrict__ ell_col, const float *__restrict__ ell_val,
                  const int64_t *__restrict__ ell_off, const float *__restrict__ h, const int64_t *__restrict__ off,
                  const int4 *__restrict__ items, int n_items, int R, const float *__restrict__ alpha_tab,
                  int alpha_len, const float *__restrict__ zscale_tab, const float *__restrict__ xscale_tab,
-                 int iters, int *__restrict__ queue) {
+                 int iters, float eps, int32_t *__restrict__ steps, int *__restrict__ queue) {
     extern __shared__ float4 res_smem4[];
     __shared__ int next;
+    __shared__ float stop_red[STOP ? 32 : 1][32];
+    __shared__ int stop_frozen[16];
+    __shared__ int stop_all;
+    const ResidentStop stop{eps, steps, stop_red, stop_frozen, &stop_all};
     while (true) {
         if (threadIdx.x == 0) next = atomicAdd(queue, 1);
         __syncthreads();  // also: every thread is done with the previous item's shared memory
@@ -275,17 +353,18 @@ batched_resident(float *__restrict__ x, const uint16_t *__restrict__ ell_col, co
         const uint16_t *ec = ell_col + eo;
         const float *ev = ell_val + eo;
         switch (it.z) {
-            case 16: resident_item<16>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
-            case 8: resident_item<8>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
-            case 4: resident_item<4>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
-            case 2: resident_item<2>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
-            default: resident_item<1>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1); break;
+            case 16: resident_item<16, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
+            case 8: resident_item<8, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
+            case 4: resident_item<4, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
+            case 2: resident_item<2, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
+            default: resident_item<1, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
         }
     }
 }
 
-ising_status_t launch_resident(ising_context *c, float *x, int R, const ParamTabs &p, int iters, cudaStream_t st) {
-    auto kern = batched_resident;
+ising_status_t launch_resident(ising_context *c, float *x, int R, const ParamTabs &p, int iters, float eps,
+                               int32_t *steps, cudaStream_t st) {
+    auto kern = eps > 0.f ? batched_resident<true> : batched_resident<false>;
     const int smem = static_cast<int>(c->batch_items_smem);
     DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
@@ -296,7 +375,7 @@ ising_status_t launch_resident(ising_context *c, float *x, int R, const ParamTab
     DOCH_CUDA(cudaMemsetAsync(c->batch_queue, 0, sizeof(int), st));
     kern<<<grid, 1024, smem, st>>>(x, c->ell_col, c->ell_val, c->ell_off, c->h_f32, c->inst_off,
                                    c->batch_items.as<int4>(), c->batch_items_count, R, p.alpha_f, p.alpha_len,
-                                   p.zscale_f, p.xscale_f, iters, c->batch_queue);
+                                   p.zscale_f, p.xscale_f, iters, eps, steps, c->batch_queue);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
@@ -310,7 +389,7 @@ static ising_status_t resident_items(ising_context *c, int R) {
     int dev = 0, optin = 0;
     DOCH_CUDA(cudaGetDevice(&dev));
     DOCH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int64_t cap = optin - 64;  // the kernel's static shared memory
+    const int64_t cap = optin - 5120;  // the kernel's static shared memory (queue slot, stopping-rule sums)
     struct Item { int64_t work; int b, g0, G; };
     std::vector<Item> items;
     size_t smem = 0;
@@ -336,13 +415,13 @@ static ising_status_t resident_items(ising_context *c, int R) {
 }
 
 ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, float eps, int32_t *steps) {
     if (!c->batch_queue || !c->ell_col || c->inst_nnz_h.size() != static_cast<size_t>(c->n_inst))
         return ISING_ERR_UNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return ISING_ERR_UNSUPPORTED;
     const ising_status_t s = resident_items(c, R);
     if (s != ISING_OK) return s;
-    return launch_resident(c, x, R, p, iters, st);
+    return launch_resident(c, x, R, p, iters, eps, steps, st);
 }
 
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,

@@ -125,3 +125,39 @@ def test_stop_batched_host_buffers_and_extremes():
     for b, g in enumerate(gs):
         ref = O.doch(O.Problem(g, hs[b]), x0[off[b]:off[b + 1]], alphas[b], betas[b], 1)
         assert _rel(x1[off[b]:off[b + 1]], ref).max() <= 1e-12
+
+
+def test_stop_batched_fp32_in_resident_kernel():
+    """Batched FP32 instances apply the rule inside the shared-memory resident kernel
+    (replica groups of 16, 8 and 2 here); eps = 0 and one-step runs reproduce
+    ising_iterate bit for bit (the same kernel with the rule off)."""
+    sizes, degrees = [500, 3000, 9000], [4, 7, 5]
+    gs = [I.regular_gauss(n, d, seed=340 + b) for b, (n, d) in enumerate(zip(sizes, degrees))]
+    hs = [I.field_gauss(g.n, 0.1, seed=350 + b).astype(np.float32) for b, g in enumerate(gs)]
+    off = np.cumsum([0] + [g.n for g in gs]).astype(np.int64)
+    nz = np.cumsum([0] + [g.nnz for g in gs])
+    rp = np.concatenate([[0]] + [g.row_ptr[1:] + z for g, z in zip(gs, nz[:-1])])
+    col = np.concatenate([g.col + o for g, o in zip(gs, off[:-1])]).astype(np.int32)
+    J = I.CSR(int(off[-1]), rp, col, np.concatenate([g.val for g in gs]).astype(np.float32))
+    h = np.concatenate(hs)
+    R = 16
+    x0 = I.x0_uniform(J.n, R, seed=360)
+    ab = [O.alpha_beta(g, eta=1.0, method="wigner") for g in gs]
+    alphas, betas = [a for a, _ in ab], [b for _, b in ab]
+    x, steps = _run(J, x0, alphas, betas, 300, 1e-4, h=h, instances=off)
+    for b, g in enumerate(gs):
+        compared, _ = _compare(O.Problem(g, hs[b]), x0[off[b]:off[b + 1]], alphas[b], betas[b], 300, 1e-4,
+                               x[off[b]:off[b + 1]], steps[b * R:(b + 1) * R], 1e-3, 1e-5)
+        assert compared >= R - 2
+    hd = N.ising_create(N.Problem(J, h, off))
+    try:
+        for iters, eps in ((20, 0.0), (1, 1e9)):
+            xa = torch.from_numpy(x0.copy()).cuda()
+            N.ising_iterate(hd, xa, alphas, betas, iters, n_instances=len(gs))
+            xb = torch.from_numpy(x0.copy()).cuda()
+            sb = torch.zeros(len(gs) * R, dtype=torch.int32, device="cuda")
+            N.ising_iterate_until(hd, xb, alphas, betas, 20, eps, steps=sb)
+            assert torch.equal(xa, xb)
+            assert (sb.cpu().numpy() == iters).all()
+    finally:
+        N.ising_destroy(hd)
