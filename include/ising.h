@@ -154,6 +154,35 @@ ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double e
  */
 ISING_API ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out);
 
+/*
+ * Algorithm S5 (Supplementary Note 9) generated on the device, straight into
+ * a new handle's CSR arrays (no host copy of J): n spins, p in percent; for
+ * every pair i > j, z in {1, ..., N_p} with N_p = floor(102300 / p), and
+ * J_ij = J_ji = z - 511 where z < 1023 (stored even when 0). The draw of pair
+ * (i, j) is value t = i (i - 1) / 2 + j of the counter-based SplitMix64
+ * stream s = mix(seed * 0x9E3779B97F4A7C15 + 13 * 0x94D049BB133111EB):
+ * u = mix(s + (t + 1) * 0x9E3779B97F4A7C15), z = 1 + floor(u N_p / 2^64).
+ * Couplings are held as int32 (integer energies are exact). Cost: n^2 draws.
+ */
+ISING_API ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int32_t flags, ising_handle_t *out);
+
+/*
+ * Eq. alphabeta on the device for a one-instance CSR or TORUS2D handle (for
+ * problems that exist only on the device): the same rule as
+ * ising_default_params (method 0 = auto, 1 = power iteration on -J +
+ * ||J||_inf I, 2 = Wigner estimate), with FP64 reductions on the device.
+ */
+ISING_API ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method, double *alpha_out,
+                                   double *beta_out);
+
+/*
+ * Copy a CSR handle's device arrays to the caller (host or device): row_ptr
+ * [n+1] int64, col [nnz] int32, val [nnz] of the storage type *jtype_out
+ * (I8, I32, F32 or F64). Any output may be NULL (nnz_out alone sizes them).
+ */
+ISING_API ising_status_t ising_csr_export(ising_handle_t h, int64_t *row_ptr, int32_t *col, void *val,
+                                int64_t *nnz_out, int32_t *jtype_out);
+
 /* Release the handle and everything it owns. NULL is accepted. */
 ISING_API void ising_destroy(ising_handle_t h);
 

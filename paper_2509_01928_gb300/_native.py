@@ -73,6 +73,10 @@ def load():
                                         ctypes.c_int32, _vp, _vp, _vp]
     lib.ising_iterate_until.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32,
                                         ctypes.c_double, _vp, _vp]
+    lib.ising_create_s5.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                    ctypes.POINTER(_vp)]
+    lib.ising_params_device.argtypes = [_vp, ctypes.c_double, ctypes.c_int32, _vp, _vp]
+    lib.ising_csr_export.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     lib.ising_energy.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     lib.ising_backward.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
@@ -88,7 +92,7 @@ def load():
     lib.ising_last_error.argtypes = []
     lib.ising_last_error.restype = ctypes.c_char_p
     for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_iterate_adoch", "ising_iterate_until",
-                 "ising_energy",
+                 "ising_energy", "ising_create_s5", "ising_params_device", "ising_csr_export",
                  "ising_backward", "ising_synchronize", "ising_get_size"):
         getattr(lib, name).restype = st
     _lib = lib
@@ -273,6 +277,40 @@ def ising_iterate_until(handle: int, x, alpha, beta, max_iters: int, eps: float,
                                       int(max_iters), float(eps), _ptr(steps), _stream(stream, x, steps)),
            "ising_iterate_until")
     return x
+
+
+def ising_create_s5(n: int, p: float, seed: int, flags: int = 0) -> int:
+    """Handle of the Algorithm S5 matrix (n spins, p percent), generated on the device."""
+    out = ctypes.c_void_p()
+    _check(load().ising_create_s5(int(n), float(p), int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), ctypes.byref(out)),
+           "ising_create_s5")
+    return out.value
+
+
+def ising_params_device(handle: int, eta: float = 1.0, method: int = 0):
+    """(alpha, beta) of Eq. alphabeta computed on the device for a one-instance handle."""
+    a = np.zeros(1)
+    b = np.zeros(1)
+    _check(load().ising_params_device(handle, float(eta), int(method), a.ctypes.data, b.ctypes.data),
+           "ising_params_device")
+    return a, b
+
+
+def ising_csr_export(handle: int):
+    """(row_ptr, col, val) of a CSR handle, copied to host numpy arrays."""
+    lib = load()
+    nnz = ctypes.c_int64()
+    jt = ctypes.c_int32()
+    _check(lib.ising_csr_export(handle, None, None, None, ctypes.byref(nnz), ctypes.byref(jt)), "ising_csr_export")
+    n = ctypes.c_int64()
+    _check(lib.ising_get_size(handle, ctypes.byref(n), None), "ising_get_size")
+    rp = np.zeros(n.value + 1, np.int64)
+    col = np.zeros(max(1, nnz.value), np.int32)
+    vdt = {I8: np.int8, I32: np.int32, F32: np.float32, F64: np.float64}[jt.value]
+    val = np.zeros(max(1, nnz.value), vdt)
+    _check(lib.ising_csr_export(handle, rp.ctypes.data, col.ctypes.data, val.ctypes.data, None, None),
+           "ising_csr_export")
+    return rp, col[:nnz.value], val[:nnz.value]
 
 
 def ising_energy(handle: int, x, E_int=None, cut_int=None, E_f64=None, cut_f64=None, best=None,

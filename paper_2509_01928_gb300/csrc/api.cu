@@ -794,6 +794,75 @@ ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handl
     return ISING_OK;
 }
 
+ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int32_t flags, ising_handle_t *out) {
+    g_err.clear();
+    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2 || n >= (int64_t(1) << 31)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^31 - 1");
+    if (!(p > 0.0) || p > 100.0) return fail(ISING_ERR_INVALID_ARG, "p (percent) must be in (0, 100]");
+    // N_p = floor(102300 / p); keep u < T = ceil(1022 * 2^64 / N_p) (exact in 128-bit integers)
+    const uint64_t np = static_cast<uint64_t>(std::floor(102300.0 / p));
+    const unsigned __int128 num = static_cast<unsigned __int128>(1022) << 64;
+    const uint64_t thr = static_cast<uint64_t>((num + np - 1) / np);
+    ising_context *c = new ising_context();
+    auto bail = [&](ising_status_t s) {
+        destroy_ctx(c);
+        return s;
+    };
+    ising_status_t s;
+    if ((s = [&]() -> ising_status_t {
+             DOCH_CUDA(cudaGetDevice(&c->device));
+             DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+             c->flags = flags;
+             c->format = ISING_FMT_CSR;
+             c->jtype = ISING_I32;
+             c->n = n;
+             c->n_inst = 1;
+             c->inst_off_h = {0, n};
+             c->max_inst_n = n;
+             c->has_h = false;
+             c->integer = true;
+             DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
+             constexpr uint64_t kTagS5 = 13;  // sub-stream tag of the S5 draws
+             DOCH_CHECK(s5_generate(c, n, s5_stream_seed(seed, kTagS5), thr, np));
+             void *ew = nullptr;
+             DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
+             c->err_word = static_cast<int *>(ew);
+             DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
+             void *eh = nullptr;
+             DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
+             c->err_host = static_cast<int *>(eh);
+             *c->err_host = 0;
+             return ISING_OK;
+         }()) != ISING_OK)
+        return bail(s);
+    *out = c;
+    return ISING_OK;
+}
+
+ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method, double *alpha_out,
+                                   double *beta_out) {
+    g_err.clear();
+    if (!h || !alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
+    if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    if (h->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "device parameters run on one instance");
+    return params_device(h, eta, method, alpha_out, beta_out);
+}
+
+ising_status_t ising_csr_export(ising_handle_t h, int64_t *row_ptr, int32_t *col, void *val, int64_t *nnz_out,
+                                int32_t *jtype_out) {
+    g_err.clear();
+    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+    if (h->format != ISING_FMT_CSR) return fail(ISING_ERR_UNSUPPORTED, "the handle does not hold CSR couplings");
+    if (nnz_out) *nnz_out = h->nnz;
+    if (jtype_out) *jtype_out = h->jtype;
+    if (row_ptr) DOCH_CUDA(cudaMemcpy(row_ptr, h->row_ptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDefault));
+    if (col && h->nnz) DOCH_CUDA(cudaMemcpy(col, h->col, sizeof(int32_t) * h->nnz, cudaMemcpyDefault));
+    if (val && h->nnz) DOCH_CUDA(cudaMemcpy(val, h->val, dtype_size(h->jtype) * h->nnz, cudaMemcpyDefault));
+    return ISING_OK;
+}
+
 void ising_destroy(ising_handle_t h) { destroy_ctx(h); }
 
 ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances) {

@@ -196,6 +196,14 @@ ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, in
 ising_status_t adoch_iterate(ising_context *c, void *x, int xtype, int R, const ParamTabs &p, int iters, int q,
                              int8_t *acc_dev, double *H_dev, cudaStream_t st);
 
+// Algorithm S5 on the device (k_gen.cu): fills c->row_ptr, col, val (I32),
+// nnz and max_row_nnz for n spins; sd = stream seed, thr = keep threshold,
+// np = N_p. s5_stream_seed(seed, tag) is the generator's stream seed.
+ising_status_t s5_generate(ising_context *c, int64_t n, uint64_t sd, uint64_t thr, uint64_t np);
+uint64_t s5_stream_seed(uint64_t seed, uint64_t tag);
+// Eq. alphabeta on the device for one instance (CSR or TORUS2D).
+ising_status_t params_device(const ising_context *c, double eta, int method, double *alpha, double *beta);
+
 // Stopping rule of Remark S2 (k_stop.cu): device state per (instance,
 // replica) pair and the kernels run after each step x^(k) -> x^(k+1).
 struct StopState {
