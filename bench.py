@@ -634,8 +634,89 @@ class Adoch:
         self.N.ising_destroy(self.h)
 
 
+class S5:
+    """Algorithm S5 matrix generated on the device (n = 1e5, p = 0.1 %, ~1e7 couplings), parameters on
+    the device, then 500 FP32 DOCH steps with R = 16 on the CSR path."""
+
+    dominant = "csr_step_kernel"
+    dtype = "f32"
+
+    def __init__(self, args, rank, N, I, torch):
+        self.n, self.p, self.R, self.iters = args.s5_n, args.s5_p, 16, args.s5_iters
+        self.N, self.torch = N, torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self.h = N.ising_create_s5(self.n, self.p, 17 + 1000 * rank, flags=N.FLAG_ASYNC)
+        t1 = time.perf_counter()
+        self.alpha, self.beta = N.ising_params_device(self.h, eta=1.0, method=2)
+        t2 = time.perf_counter()
+        rp, _, _ = N.ising_csr_export(self.h)
+        self.nnz = int(rp[-1])
+        self.x0 = I.x0_uniform(self.n, self.R, seed=18 + 1000 * rank)
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        self.launches = self.iters + 3
+        self.config = {"workload": f"Algorithm S5 n={self.n} p={self.p}% (9-bit couplings, {self.nnz} stored "
+                                   f"entries) generated on the device, Wigner parameters on the device, R={self.R} "
+                                   f"FP32, {self.iters} DOCH steps + sign + int64 energy",
+                       "n": self.n, "nnz": self.nnz, "replicas": self.R, "iters": self.iters,
+                       "generate_ms": 1e3 * (t1 - t0), "params_ms": 1e3 * (t2 - t1),
+                       "l2": "iterate (6.4 MB) L2-resident; couplings (80 MB) streamed; no flush"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, stream=sid)
+
+    def roofline(self, per_launch_s):
+        peak, kind = measured_peaks()
+        # per step from HBM: col 4 B + val 4 B per stored entry, x read and written once
+        alg = 8 * self.nnz + 2 * self.n * self.R * 4
+        ach = alg / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": kind, "algorithmic_bytes_per_launch": alg,
+                "note": "the neighbour gathers (nnz x R x 4 B per step) are served from L2 and not counted"}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        Eh = np.zeros(self.R, np.int64)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh, self.alpha, self.beta, self.iters, stream=sid)
+            N.ising_energy(self.h, xh, E_int=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 4
+        return dt, 2 * nb, nb + 8 * self.R, "ising_iterate + ising_energy on pinned host arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        n, p, iters = 20000, 0.1, 200
+        J = I.s5_csr(n, p, seed=17)
+        x0 = I.x0_uniform(n, self.R, seed=18, dtype=np.float64)
+        a, b = O.alpha_beta(J, eta=1.0, method="wigner")
+        P = O.Problem(J)
+        t0 = time.perf_counter()
+        O.doch(P, x0, a, b, iters)
+        dt = time.perf_counter() - t0
+        return {"value": n * self.R * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"Algorithm S5 n={n} p={p}%, R={self.R}, {iters} FP64 DOCH steps"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
 WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800,
-             "adoch": Adoch}
+             "adoch": Adoch, "s5": S5}
 
 
 def run_ours(args):
@@ -751,12 +832,16 @@ def main():
     ap.add_argument("--workload", default="torus", choices=sorted(WORKLOADS),
                     help="torus (default: 10^4 x 10^4 lattice), dense (16384 x 256 on tcgen05), "
                          "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64), "
-                         "adoch (Algorithm 2 on the 10^4 x 10^4 lattice)")
+                         "adoch (Algorithm 2 on the 10^4 x 10^4 lattice), s5 (Algorithm S5 matrix generated on "
+                         "the device, n = 1e5)")
     ap.add_argument("--dense-n", type=int, default=16384)
     ap.add_argument("--dense-iters", type=int, default=1000)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--adoch-iters", type=int, default=100)
+    ap.add_argument("--s5-n", type=int, default=100000)
+    ap.add_argument("--s5-p", type=float, default=0.1)
+    ap.add_argument("--s5-iters", type=int, default=500)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
