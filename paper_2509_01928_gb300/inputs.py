@@ -377,3 +377,16 @@ def s5_csr(n: int, p: float, seed: int) -> CSR:
         i = j = np.zeros(0, np.int64)
         v = np.zeros(0, np.int16)
     return csr_from_upper(n, j, i, v)
+
+
+# ---------------------------------------------------------------------------
+# Procedural dense couplings (Supplementary Note 9)
+# ---------------------------------------------------------------------------
+
+def procedural_sin(n: int, offset: float = 100.0) -> np.ndarray:
+    """Dense J_ij = sin(i j + offset) for 1-based i != j, J_ii = 0 (FP64; the
+    argument i j + offset is an exact double for i j < 2^53)."""
+    idx = np.arange(1, n + 1, dtype=np.float64)
+    J = np.sin(np.outer(idx, idx) + offset)
+    np.fill_diagonal(J, 0.0)
+    return J
