@@ -67,7 +67,9 @@ typedef enum {
 typedef enum {
     ISING_FMT_CSR = 0,     /* compressed sparse rows (Supplementary Note 9)            */
     ISING_FMT_TORUS2D = 1, /* periodic 2-D lattice, one coupling per lattice edge      */
-    ISING_FMT_DENSE = 2    /* full n x n row-major matrix                               */
+    ISING_FMT_DENSE = 2,   /* full n x n row-major matrix                               */
+    ISING_FMT_PROCEDURAL = 3 /* J_ij = sin(i j + c), generated on the fly (handles from
+                                ising_create_procedural only)                           */
 } ising_format_t;
 
 /* Element types. */
@@ -167,10 +169,29 @@ ISING_API ising_status_t ising_create(const ising_problem_t *p, int32_t flags, i
 ISING_API ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int32_t flags, ising_handle_t *out);
 
 /*
+ * Procedural dense couplings of Supplementary Note 9 (the benchmark matrix of
+ * the paper's 10^6- and 10^7-spin fully connected runs): J_ij = sin(i j + c)
+ * for 1-based indices i != j, J_ii = 0, no field. Nothing of J is stored: the
+ * kernels generate every coupling where it is used (Algorithm S6's blocks, on
+ * one GPU), n^2 sines per coupling product, from an exact integer phase and
+ * the hardware sine (each coupling within about 1e-6 of the exact value).
+ *   n       2 .. 2^30 spins;  c  0 .. 2^40 (the paper uses 100).
+ * The handle supports ising_iterate (F32 iterates, no H_trace),
+ * ising_iterate_until (F32), ising_energy (E_f64, cut_f64, best, spins; the
+ * sum of J in the cut is evaluated in closed form in FP64) and
+ * ising_params_device (Wigner estimate; method 1 is ISING_ERR_UNSUPPORTED).
+ * Creation costs O(n) host work (closed-form sums of J and J^2).
+ */
+ISING_API ising_status_t ising_create_procedural(int64_t n, int64_t c, int32_t flags, ising_handle_t *out);
+
+/*
  * Eq. alphabeta on the device for a one-instance CSR or TORUS2D handle (for
  * problems that exist only on the device): the same rule as
  * ising_default_params (method 0 = auto, 1 = power iteration on -J +
  * ||J||_inf I, 2 = Wigner estimate), with FP64 reductions on the device.
+ * PROCEDURAL handles take the Wigner estimate for methods 0 and 2, with the
+ * sums of J and J^2 in closed form and the row sums of |J_ij| from one pass
+ * over the generated couplings.
  */
 ISING_API ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method, double *alpha_out,
                                    double *beta_out);
@@ -200,7 +221,8 @@ ISING_API void ising_destroy(ising_handle_t h);
  *          alpha of step k (the last step's for k = iters). Computed in FP64
  *          on the device, fused into the iteration kernel.
  * For DENSE the iterate is BF16 and the coupling product runs on the
- * tcgen05 tensor cores with FP32 accumulation.
+ * tcgen05 tensor cores with FP32 accumulation. For PROCEDURAL the iterate is
+ * F32, H_trace must be NULL, and each step generates all n^2 couplings.
  */
 ISING_API ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                              const double *alpha, int32_t alpha_len, const double *beta,
@@ -247,8 +269,8 @@ ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t 
  * the rule inside it (FP32 sums per thread and warp, FP64 across warps) and
  * end each instance's replica group once all of its replicas stopped;
  * otherwise the host checks every 8 steps whether any pair still runs and
- * ends the loop when none does. CSR and TORUS2D; ISING_ERR_UNSUPPORTED for
- * DENSE.
+ * ends the loop when none does. CSR, TORUS2D and PROCEDURAL (F32);
+ * ISING_ERR_UNSUPPORTED for DENSE.
  */
 ISING_API ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                                    const double *alpha, const double *beta, int32_t max_iters, double eps,

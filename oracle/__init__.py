@@ -11,6 +11,8 @@ What each part restates (arXiv 2509.01928):
   * ``doch``          -- Algorithm 1 with the operator T of Eq. FPE.
   * ``hamiltonian``   -- Eq. Hamilton (H = f - g), with -h^T x for a field.
   * ``energy``        -- Eq. IsingModel; ``cut`` per Supplementary Note 5 (W = -2J).
+  * ``procedural_rows`` -- rows of J x for J_ij = sin(i j + c) (Supplementary
+                         Note 9), 1-based indices, J_ii = 0.
   * ``backward``      -- adjoint of N steps of Eq. FPE (derived; the paper has none).
   * ``alpha_beta``    -- Eq. alphabeta; lambda_max by a dense symmetric
                          eigensolver, or by the Wigner estimate of Eq.
@@ -24,7 +26,8 @@ Readings of the paper used here (where it is silent or ambiguous):
   * <J> in the Wigner estimate is the standard deviation of the n(n-1)
     off-diagonal entries (zeros included);
   * alpha_max uses lambda_max(-J) as in Eq. alphabeta;
-  * the ADOCH window is H(x^(max(0,k-q))) .. H(x^(k)).
+  * the ADOCH window is H(x^(max(0,k-q))) .. H(x^(k));
+  * the procedural matrix sin(i j + c) counts i and j from 1 and has J_ii = 0.
 """
 from __future__ import annotations
 
@@ -183,6 +186,21 @@ def coupling_product(p: Problem, x) -> np.ndarray:
     u = np.empty_like(x)
     _load().orc_coupling_product(p.ref, x.shape[1], _ptr(x, _dp), _ptr(u, _dp))
     return u
+
+
+def procedural_rows(n: int, c: int, rows, x) -> np.ndarray:
+    """u_i = sum_{j != i} sin(i j + c) x_j for the listed 0-based rows of the
+    procedural matrix of Supplementary Note 9 (1-based i, j in the formula),
+    one row at a time in FP64 (i j + c is an exact double below 2^53).
+    x: [n][R]; returns [len(rows)][R]."""
+    x = _state(x, n)
+    cols = np.arange(1, n + 1, dtype=np.float64)
+    out = np.empty((len(rows), x.shape[1]))
+    for k, i in enumerate(rows):
+        w = np.sin((i + 1) * cols + float(c))
+        w[i] = 0.0
+        out[k] = w @ x
+    return out
 
 
 def hamiltonian(p: Problem, x, alpha: float, beta: float) -> np.ndarray:

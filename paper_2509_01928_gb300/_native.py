@@ -24,7 +24,7 @@ STATUS_NAMES = {
     6: "ISING_ERR_OOM", 7: "ISING_ERR_CUDA", 8: "ISING_ERR_TIMEOUT", 9: "ISING_ERR_NOT_MONOTONE",
     10: "ISING_ERR_UNSUPPORTED",
 }
-FMT_CSR, FMT_TORUS2D, FMT_DENSE = 0, 1, 2
+FMT_CSR, FMT_TORUS2D, FMT_DENSE, FMT_PROCEDURAL = 0, 1, 2, 3
 I8, I16, I32, FP8E4M3, BF16, F32, F64 = range(7)
 FLAG_ASYNC, FLAG_SKIP_VALIDATION, FLAG_STRICT_MONOTONE, FLAG_SINGLE_STEP = 1, 2, 4, 8
 
@@ -75,6 +75,7 @@ def load():
                                         ctypes.c_double, _vp, _vp]
     lib.ising_create_s5.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
                                     ctypes.POINTER(_vp)]
+    lib.ising_create_procedural.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_vp)]
     lib.ising_params_device.argtypes = [_vp, ctypes.c_double, ctypes.c_int32, _vp, _vp]
     lib.ising_csr_export.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     lib.ising_energy.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -92,7 +93,7 @@ def load():
     lib.ising_last_error.argtypes = []
     lib.ising_last_error.restype = ctypes.c_char_p
     for name in ("ising_default_params", "ising_create", "ising_iterate", "ising_iterate_adoch", "ising_iterate_until",
-                 "ising_energy", "ising_create_s5", "ising_params_device", "ising_csr_export",
+                 "ising_energy", "ising_create_s5", "ising_create_procedural", "ising_params_device", "ising_csr_export",
                  "ising_backward", "ising_synchronize", "ising_get_size"):
         getattr(lib, name).restype = st
     _lib = lib
@@ -284,6 +285,13 @@ def ising_create_s5(n: int, p: float, seed: int, flags: int = 0) -> int:
     out = ctypes.c_void_p()
     _check(load().ising_create_s5(int(n), float(p), int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), ctypes.byref(out)),
            "ising_create_s5")
+    return out.value
+
+
+def ising_create_procedural(n: int, c: int = 100, flags: int = 0) -> int:
+    """Handle of the procedural dense couplings J_ij = sin(i j + c) (1-based, J_ii = 0)."""
+    out = ctypes.c_void_p()
+    _check(load().ising_create_procedural(int(n), int(c), int(flags), ctypes.byref(out)), "ising_create_procedural")
     return out.value
 
 

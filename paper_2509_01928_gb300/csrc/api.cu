@@ -613,6 +613,9 @@ ising_status_t step(ising_context *c, const void *xi, void *xo, int xtype, int R
                               beta_h[0], st);
     }
     if (c->format == ISING_FMT_CSR) return csr_step(c, xi, xo, xtype, R, p, k, st);
+    if (c->format == ISING_FMT_PROCEDURAL)
+        return proc_step(c, static_cast<const float *>(xi), static_cast<float *>(xo), R,
+                         alpha_h[p.alpha_len == 1 ? 0 : k], 1.0 / beta_h[0], st);
     return fail(ISING_ERR_UNSUPPORTED, "this storage form has no iteration kernel yet");
 }
 
@@ -840,6 +843,46 @@ ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int32_t flags
     return ISING_OK;
 }
 
+ising_status_t ising_create_procedural(int64_t n, int64_t cst, int32_t flags, ising_handle_t *out) {
+    g_err.clear();
+    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > (int64_t(1) << 30)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^30");
+    if (cst < 0 || cst > (int64_t(1) << 40)) return fail(ISING_ERR_INVALID_ARG, "c must be in 0 .. 2^40");
+    ising_context *c = new ising_context();
+    ising_status_t s = [&]() -> ising_status_t {
+        DOCH_CUDA(cudaGetDevice(&c->device));
+        DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+        c->flags = flags;
+        c->format = ISING_FMT_PROCEDURAL;
+        c->jtype = ISING_F32;
+        c->n = n;
+        c->n_inst = 1;
+        c->inst_off_h = {0, n};
+        c->max_inst_n = n;
+        c->has_h = false;
+        c->integer = false;
+        c->proc_offset = cst;
+        proc_closed_sums(n, cst, &c->proc_s1, &c->proc_s2);
+        DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
+        void *ew = nullptr;
+        DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
+        c->err_word = static_cast<int *>(ew);
+        DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
+        void *eh = nullptr;
+        DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
+        c->err_host = static_cast<int *>(eh);
+        *c->err_host = 0;
+        return ISING_OK;
+    }();
+    if (s != ISING_OK) {
+        destroy_ctx(c);
+        return s;
+    }
+    *out = c;
+    return ISING_OK;
+}
+
 ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method, double *alpha_out,
                                    double *beta_out) {
     g_err.clear();
@@ -847,6 +890,10 @@ ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method,
     if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
     if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
     if (h->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "device parameters run on one instance");
+    if (h->format == ISING_FMT_PROCEDURAL) {
+        if (method == 1) return fail(ISING_ERR_UNSUPPORTED, "PROCEDURAL couplings take the Wigner estimate");
+        return proc_params(h, eta, alpha_out, beta_out);
+    }
     return params_device(h, eta, method, alpha_out, beta_out);
 }
 
@@ -886,6 +933,9 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
     if (alpha_len != 1 && alpha_len != iters) return fail(ISING_ERR_INVALID_ARG, "alpha_len must be 1 or iters");
     if (h->format == ISING_FMT_DENSE) {
         if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
+    } else if (h->format == ISING_FMT_PROCEDURAL) {
+        if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+        if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for PROCEDURAL couplings");
     } else if (xtype != ISING_F32 && xtype != ISING_F64) {
         return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
     }
@@ -1053,7 +1103,10 @@ ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int
     if (!std::isfinite(eps) || eps < 0.0) return fail(ISING_ERR_INVALID_ARG, "eps must be finite and >= 0");
     if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
     ising_context *c = h;
-    if (c->format == ISING_FMT_DENSE) return fail(ISING_ERR_UNSUPPORTED, "the stopping rule runs on CSR or TORUS2D");
+    if (c->format == ISING_FMT_DENSE)
+        return fail(ISING_ERR_UNSUPPORTED, "the stopping rule runs on CSR, TORUS2D or PROCEDURAL");
+    if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
+        return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t count = c->n * R;
     const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
@@ -1165,6 +1218,8 @@ ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int3
     int32_t *Bd = reinterpret_cast<int32_t *>(Cd + pairs);
     if (c->format == ISING_FMT_DENSE)
         DOCH_CHECK(dense_energy(c, xd, xtype, R, Ei, Ci, Ed, Cd, st));
+    else if (c->format == ISING_FMT_PROCEDURAL)
+        DOCH_CHECK(proc_energy(c, xd, xtype, R, Ed, Cd, st));
     else
         DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
     if (best) DOCH_CHECK(best_replica(c, c->integer ? Ei : nullptr, Ed, R, Bd, st));

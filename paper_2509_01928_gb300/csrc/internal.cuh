@@ -91,6 +91,10 @@ struct ising_context {
     int dense_type = 0;
     int64_t dense_ld = 0;
     long long dense_jsum = 0;  // sum_ij J_ij, for the cut
+    // PROCEDURAL: J_ij = sin(i j + proc_offset) (1-based, J_ii = 0), generated on
+    // the fly; proc_s1 / proc_s2 = sums of J_ij and J_ij^2 over i != j (FP64)
+    int64_t proc_offset = 0;
+    double proc_s1 = 0.0, proc_s2 = 0.0;
     // field (both precisions; integer copy when integral)
     float *h_f32 = nullptr;
     double *h_f64 = nullptr;
@@ -236,6 +240,16 @@ ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alp
                              double beta, int iters, cudaStream_t st);
 ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
                             double *E_d, double *cut_d, cudaStream_t st);
+
+// Procedural couplings (k_proc.cu), FP32 iterates, one instance, no field.
+// One DOCH step x_out = T(x_in); energies into E_d / cut_d (device, R each);
+// Eq. alphabeta with the Wigner estimate; the closed-form sums of J and J^2.
+ising_status_t proc_step(ising_context *c, const float *x_in, float *x_out, int R, double alpha, double inv_beta,
+                         cudaStream_t st);
+ising_status_t proc_energy(ising_context *c, const void *x, int xtype, int R, double *E_d, double *cut_d,
+                           cudaStream_t st);
+ising_status_t proc_params(const ising_context *c, double eta, double *alpha, double *beta);
+void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2);
 
 // Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
 // (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss

@@ -1,0 +1,394 @@
+// Procedural dense couplings (Supplementary Note 9, on one GPU the block
+// product of Algorithm S6): J_ij = sin(i j + c) for 1-based i != j, J_ii = 0,
+// generated where they are used and never stored.
+//
+// Phase. With F = floor(2^96 / (2 pi)), the 96-bit integer (a F) mod 2^96 is
+// frac(a / (2 pi)) 2^96 to within a units (a fixed-point argument reduction in
+// the manner of Payne and Hanek, exact in integers). Along row i the phase of
+// column j + 1 is that of column j plus (i F) mod 2^96; the kernels keep the top
+// 64 bits of both (the truncation adds at most one 2^-64 turn per column) and
+// advance four columns at a time on four independent chains.
+// Coupling. With s the top 32 bits of the phase as a signed integer, the
+// angle is pi y for y = s / 2^31 in [-1, 1), and sin(pi y) = sign(y)
+// cos(pi (|y| - 1/2)) with pi (|y| - 1/2) in [-pi/2, pi/2]; the cosine is an
+// even polynomial of degree 10 in that argument whose coefficients minimise
+// the largest absolute error on the interval (Remez exchange; 2.2e-10 before
+// rounding). Measured against the FP64 sine of the exact phase, the FP32
+// couplings are within 1.7e-7 (rms 3.0e-8), about the rounding of J to FP32.
+// Product. One thread per row, CTAs of kPT rows, the columns in tiles of kPN
+// staged in shared memory (each value read by all threads: a broadcast);
+// per-tile sums, then a sum over the tiles of a column split. The splits
+// (blockIdx.y) give enough CTAs to fill the GPU for any n; their partial sums
+// go to a scratch array [split][n][R] that a finishing kernel adds in split
+// order, so results do not depend on the schedule.
+// The sums of J and of J^2 over i != j (for the cut and the Wigner estimate)
+// come in closed form from geometric series of the sines, in FP64 on the host;
+// the rows' sums of |J_ij| (Eq. alphabeta) from a device pass.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cbrt.cuh"
+#include "internal.cuh"
+
+namespace doch {
+namespace {
+
+constexpr int kPT = 256;  // rows per CTA (one per thread)
+constexpr int kPN = 256;  // columns per shared-memory tile (kPN == kPT: one diagonal tile per CTA)
+
+// top 64 bits of (a G) mod 2^96 for the 96-bit constant G = (g2, g1, g0)
+__host__ __device__ __forceinline__ uint64_t mulmod96_top(uint64_t a, uint32_t g2, uint32_t g1, uint32_t g0) {
+    const uint64_t a0 = a & 0xFFFFFFFFull, a1 = a >> 32;
+    const uint64_t c0 = a0 * g0;
+    const uint64_t s1 = a0 * g1 + (c0 >> 32);
+    const uint64_t s2 = a1 * g0 + (s1 & 0xFFFFFFFFull);
+    const uint32_t w2 = static_cast<uint32_t>(a0 * g2 + a1 * g1 + (s1 >> 32) + (s2 >> 32));
+    return (static_cast<uint64_t>(w2) << 32) | (s2 & 0xFFFFFFFFull);
+}
+
+// floor(2^96 / (2 pi)): the phase of an integer argument in turns
+__host__ __device__ __forceinline__ uint64_t phase64(uint64_t a) {
+    return mulmod96_top(a, 0x28BE60DBu, 0x9391054Au, 0x7F09D5F4u);
+}
+
+// J for the phase p: sin(pi y) = sign(y) cos(pi (|y| - 1/2)), y = s / 2^31
+__device__ __forceinline__ float coupling(uint64_t p) {
+    const int32_t s = static_cast<int32_t>(p >> 32);
+    const float v = static_cast<float>(abs(s) - 0x40000000);  // (|y| - 1/2) 2^31 (|INT_MIN| wraps to the same angle)
+    const float u = v * v * 2.1401293066467156e-18f;          // (pi (|y| - 1/2))^2
+    float q = -2.6051495269991556e-07f;
+    q = fmaf(q, u, 2.476016135530425e-05f);
+    q = fmaf(q, u, -0.001388836140031622f);
+    q = fmaf(q, u, 0.04166663625807217f);
+    q = fmaf(q, u, -0.499999993584718f);
+    q = fmaf(q, u, 0.999999999780652f);
+    return __uint_as_float(__float_as_uint(q) ^ (static_cast<uint32_t>(s) & 0x80000000u));
+}
+
+// One kPN-column tile for RC replicas: tacc[r] = sum_j J_ij x_jr. P[4] are
+// the phases of the next four columns, advanced by D4 = 4 D per group. For
+// RC <= 2 each of the four column chains has its own sums (64 terms each,
+// added pairwise at the end), which shortens the FP32 summation; wider
+// replica groups sum the tile in one chain per replica.
+template <int RC, bool DIAG>
+__device__ __forceinline__ void tile_pass(const float *__restrict__ tf, uint64_t (&P)[4], uint64_t D4,
+                                          float (&tacc)[RC], int diag_col) {
+    constexpr int kCh = RC <= 2 ? 4 : 1;
+    float ch[kCh][RC];
+#pragma unroll
+    for (int k = 0; k < kCh; ++k)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) ch[k][r] = 0.f;
+#pragma unroll 2
+    for (int jj = 0; jj < kPN; jj += 4) {
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            w[u] = coupling(P[u]);
+            P[u] += D4;
+            if (DIAG && jj + u == diag_col) w[u] = 0.f;
+        }
+        if constexpr (RC < 4) {
+            float v[4 * RC];
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                const float4 g = reinterpret_cast<const float4 *>(tf + jj * RC)[q];
+                v[4 * q] = g.x;
+                v[4 * q + 1] = g.y;
+                v[4 * q + 2] = g.z;
+                v[4 * q + 3] = g.w;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) ch[u % kCh][r] = fmaf(w[u], v[u * RC + r], ch[u % kCh][r]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int q = 0; q < RC / 4; ++q) {
+                    const float4 g = reinterpret_cast<const float4 *>(tf + (jj + u) * RC)[q];
+                    ch[0][4 * q] = fmaf(w[u], g.x, ch[0][4 * q]);
+                    ch[0][4 * q + 1] = fmaf(w[u], g.y, ch[0][4 * q + 1]);
+                    ch[0][4 * q + 2] = fmaf(w[u], g.z, ch[0][4 * q + 2]);
+                    ch[0][4 * q + 3] = fmaf(w[u], g.w, ch[0][4 * q + 3]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        if constexpr (kCh == 4) tacc[r] = (ch[0][r] + ch[1][r]) + (ch[2][r] + ch[3][r]);
+        else tacc[r] = ch[0][r];
+    }
+}
+
+// part[split][i][rc0 + r] = sum over the split's columns j != i of J_ij x_j(rc0 + r).
+// XT = float (iterates) or int8_t (spins).
+template <int RC, typename XT>
+__global__ void __launch_bounds__(kPT)
+proc_partial(const XT *__restrict__ x, float *__restrict__ part, int64_t n, int R, int rc0, int64_t offset,
+             int tiles_per_split, int n_tiles) {
+    __shared__ __align__(16) float tf[kPN * RC];
+    const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kPT;
+    const int64_t i = row0 + threadIdx.x;
+    const int t0 = static_cast<int>(blockIdx.y) * tiles_per_split;
+    const int t1 = min(n_tiles, t0 + tiles_per_split);
+    const uint64_t i1 = static_cast<uint64_t>(i) + 1;
+    const uint64_t D = phase64(i1);
+    uint64_t P[4];
+    P[0] = phase64(i1 * (static_cast<uint64_t>(t0) * kPN + 1) + static_cast<uint64_t>(offset));
+    P[1] = P[0] + D;
+    P[2] = P[1] + D;
+    P[3] = P[2] + D;
+    const uint64_t D4 = 4 * D;
+    float acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = 0.f;
+    const int rcn = min(RC, R - rc0);
+    for (int t = t0; t < t1; ++t) {
+        const int64_t j0 = static_cast<int64_t>(t) * kPN;
+        __syncthreads();
+        for (int e = threadIdx.x; e < kPN * RC; e += kPT) {
+            const int jj = e / RC, r = e - jj * RC;
+            const int64_t j = j0 + jj;
+            float v = 0.f;
+            if (j < n && r < rcn) v = static_cast<float>(x[j * R + rc0 + r]);
+            tf[e] = v;
+        }
+        __syncthreads();
+        float tacc[RC];
+        if (j0 == row0) tile_pass<RC, true>(tf, P, D4, tacc, threadIdx.x);
+        else tile_pass<RC, false>(tf, P, D4, tacc, -1);
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[r] += tacc[r];
+    }
+    if (i >= n) return;
+    float *dst = part + (static_cast<int64_t>(blockIdx.y) * n + i) * R + rc0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+        if (r < rcn) dst[r] = acc[r];
+}
+
+// x_out = cbrt((u + alpha x) / beta) with u = sum of the split partials (in split order)
+__global__ void proc_finish_step(const float *__restrict__ part, int S, const float *__restrict__ x,
+                                 float *__restrict__ xo, int64_t count, float alpha, float zs, float xsc) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float u = part[e];
+        for (int s = 1; s < S; ++s) u += part[static_cast<int64_t>(s) * count + e];
+        xo[e] = cbrt_pow2((u + alpha * x[e]) * zs) * xsc;
+    }
+}
+
+constexpr int kQT = 256;
+
+// qpart[r][block] = sum over the block's rows of s_ir u_ir in FP64 (fixed order)
+__global__ void __launch_bounds__(kQT)
+proc_finish_quad(const float *__restrict__ part, int S, const int8_t *__restrict__ s, int64_t n, int R,
+                 double *__restrict__ qpart) {
+    const int r = blockIdx.y;
+    const int64_t count = n * R;
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = static_cast<int64_t>(blockIdx.x) * rows_per, hi = min(n, lo + rows_per);
+    double q = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kQT) {
+        const int64_t e = i * R + r;
+        float u = part[e];
+        for (int k = 1; k < S; ++k) u += part[static_cast<int64_t>(k) * count + e];
+        q += static_cast<double>(s[e]) * static_cast<double>(u);
+    }
+    __shared__ double red[kQT];
+    red[threadIdx.x] = q;
+    __syncthreads();
+    for (int w = kQT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) qpart[static_cast<int64_t>(r) * gridDim.x + blockIdx.x] = red[0];
+}
+
+// per block: max over its rows of sum_{j != i} |J_ij| (per-tile FP32 sums, FP64 across tiles)
+__global__ void __launch_bounds__(kPT)
+proc_rowabs(int64_t n, int64_t offset, int n_tiles, double *__restrict__ bmax) {
+    const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kPT;
+    const int64_t i = row0 + threadIdx.x;
+    const uint64_t i1 = static_cast<uint64_t>(i) + 1;
+    const uint64_t D = phase64(i1);
+    uint64_t P = phase64(i1 + static_cast<uint64_t>(offset));
+    double a = 0.0;
+    for (int t = 0; t < n_tiles; ++t) {
+        const int64_t j0 = static_cast<int64_t>(t) * kPN;
+        const int cols = n - j0 < kPN ? static_cast<int>(n - j0) : kPN;
+        float ta = 0.f;
+        for (int jj = 0; jj < cols; ++jj) {
+            const float w = fabsf(coupling(P));
+            P += D;
+            ta += (j0 + jj == i) ? 0.f : w;
+        }
+        a += ta;
+    }
+    __shared__ double red[kPT];
+    red[threadIdx.x] = i < n ? a : 0.0;
+    __syncthreads();
+    for (int w = kPT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bmax[blockIdx.x] = red[0];
+}
+
+struct SplitPlan {
+    int row_blocks, n_tiles, tiles_per_split, S;
+};
+
+SplitPlan plan_splits(const ising_context *c) {
+    SplitPlan p;
+    p.row_blocks = static_cast<int>((c->n + kPT - 1) / kPT);
+    p.n_tiles = static_cast<int>((c->n + kPN - 1) / kPN);
+    // at least 16 CTAs per SM over the whole launch (so the last wave is a small share)
+    const int64_t want = 16LL * c->num_sms;
+    int S = static_cast<int>(std::min<int64_t>((want + p.row_blocks - 1) / p.row_blocks, p.n_tiles));
+    S = std::max(1, std::min(S, 65535));
+    p.tiles_per_split = (p.n_tiles + S - 1) / S;
+    p.S = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
+    return p;
+}
+
+// the partial products of every replica chunk into part [S][n][R]
+template <typename XT>
+ising_status_t proc_products(const ising_context *c, const XT *x, float *part, int R, const SplitPlan &pl,
+                             cudaStream_t st) {
+    const dim3 grid(static_cast<unsigned>(pl.row_blocks), static_cast<unsigned>(pl.S));
+    for (int rc0 = 0; rc0 < R; rc0 += 16) {
+        const int left = R - rc0;
+#define DOCH_PROC_LAUNCH(RCV)                                                                                 \
+    proc_partial<RCV, XT><<<grid, kPT, 0, st>>>(x, part, c->n, R, rc0, c->proc_offset, pl.tiles_per_split, \
+                                                pl.n_tiles)
+        if (left == 1) DOCH_PROC_LAUNCH(1);
+        else if (left == 2) DOCH_PROC_LAUNCH(2);
+        else if (left <= 4) DOCH_PROC_LAUNCH(4);
+        else if (left <= 8) DOCH_PROC_LAUNCH(8);
+        else DOCH_PROC_LAUNCH(16);
+#undef DOCH_PROC_LAUNCH
+        DOCH_CUDA(cudaGetLastError());
+    }
+    return ISING_OK;
+}
+
+int stream_blocks(const ising_context *c, int64_t count) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 8LL * c->num_sms)));
+}
+
+// m/2 radians for an integer m < 2^64, reduced to [-pi, pi): the turn
+// fraction m / (4 pi) from floor(2^96 / (4 pi)) in integers
+double half_angle(uint64_t m) {
+    const uint64_t top = mulmod96_top(m, 0x145F306Du, 0xC9C882A5u, 0x3F84EAFAu);
+    return static_cast<double>(static_cast<int64_t>(top)) * (6.283185307179586476925 / 18446744073709551616.0);
+}
+
+struct Neumaier {
+    double s = 0.0, c = 0.0;
+    void add(double v) {
+        const double t = s + v;
+        c += std::fabs(s) >= std::fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    double value() const { return s + c; }
+};
+
+}  // namespace
+
+// sum_{i != j} J_ij and sum_{i != j} J_ij^2 by the geometric series
+//   sum_{j=1..n} sin(c + j i) = sin(c + (n+1) i / 2) sin(n i / 2) / sin(i / 2),
+//   sum_{j=1..n} cos(2c + 2 j i) = cos(2c + (n+1) i) sin(n i) / sin(i),
+// with J_ij^2 = (1 - cos(2 i j + 2 c)) / 2, less the diagonal terms.
+void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2) {
+    Neumaier a, b;
+    const uint64_t un = static_cast<uint64_t>(n), uc = static_cast<uint64_t>(c);
+    for (uint64_t i = 1; i <= un; ++i) {
+        const uint64_t m_sum = 2 * uc + (un + 1) * i;  // c + (n+1) i / 2 in half radians
+        const double rs = std::sin(half_angle(m_sum)) * std::sin(half_angle(un * i)) / std::sin(half_angle(i));
+        const double rc = std::cos(half_angle(2 * m_sum)) * std::sin(half_angle(2 * un * i)) /
+                          std::sin(half_angle(2 * i));
+        const uint64_t m_d = 2 * (i * i + uc);
+        a.add(rs - std::sin(half_angle(m_d)));
+        b.add(rc - std::cos(half_angle(2 * m_d)));
+    }
+    *s1 = a.value();
+    *s2 = 0.5 * (static_cast<double>(n) * (static_cast<double>(n) - 1.0) - b.value());
+}
+
+ising_status_t proc_step(ising_context *c, const float *x_in, float *x_out, int R, double alpha, double inv_beta,
+                         cudaStream_t st) {
+    const SplitPlan pl = plan_splits(c);
+    const int64_t count = c->n * R;
+    DOCH_CHECK(c->partials.ensure(sizeof(float) * count * pl.S));
+    float *part = c->partials.as<float>();
+    DOCH_CHECK(proc_products<float>(c, x_in, part, R, pl, st));
+    const int k = cbrt_prescale_exp(inv_beta);
+    const float zs = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+    const float xsc = std::ldexp(1.0f, -k);
+    proc_finish_step<<<stream_blocks(c, count), 256, 0, st>>>(part, pl.S, x_in, x_out, count,
+                                                             static_cast<float>(alpha), zs, xsc);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+// E = -1/2 s^T J s and cut = -1/2 (sum_{i != j} J_ij - s^T J s) per replica, into
+// E_d and cut_d (device, R each)
+ising_status_t proc_energy(ising_context *c, const void *x, int xtype, int R, double *E_d, double *cut_d,
+                           cudaStream_t st) {
+    const SplitPlan pl = plan_splits(c);
+    const int64_t count = c->n * R;
+    const int qb = static_cast<int>(std::min<int64_t>((c->n + kQT - 1) / kQT, 64));
+    const size_t part_b = (sizeof(float) * count * pl.S + 255) & ~size_t(255);
+    const size_t spin_b = (static_cast<size_t>(count) + 255) & ~size_t(255);
+    DOCH_CHECK(c->partials.ensure(part_b + spin_b + sizeof(double) * R * qb));
+    float *part = c->partials.as<float>();
+    int8_t *s = reinterpret_cast<int8_t *>(c->partials.as<unsigned char>() + part_b);
+    double *qp = reinterpret_cast<double *>(c->partials.as<unsigned char>() + part_b + spin_b);
+    DOCH_CHECK(write_spins(c, x, xtype, R, s, st));
+    DOCH_CHECK(proc_products<int8_t>(c, s, part, R, pl, st));
+    proc_finish_quad<<<dim3(qb, R), kQT, 0, st>>>(part, pl.S, s, c->n, R, qp);
+    DOCH_CUDA(cudaGetLastError());
+    std::vector<double> qh(static_cast<size_t>(R) * qb);
+    DOCH_CUDA(cudaMemcpyAsync(qh.data(), qp, sizeof(double) * qh.size(), cudaMemcpyDeviceToHost, st));
+    DOCH_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> E(R), cut(R);
+    for (int r = 0; r < R; ++r) {
+        double q = 0.0;
+        for (int b = 0; b < qb; ++b) q += qh[static_cast<size_t>(r) * qb + b];
+        E[r] = -0.5 * q;
+        cut[r] = -0.5 * (c->proc_s1 - q);
+    }
+    DOCH_CUDA(cudaMemcpyAsync(E_d, E.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+    DOCH_CUDA(cudaMemcpyAsync(cut_d, cut.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+    DOCH_CUDA(cudaStreamSynchronize(st));
+    return ISING_OK;
+}
+
+// Eq. alphabeta with the Wigner estimate of Eq. estimate_eig_J
+ising_status_t proc_params(const ising_context *c, double eta, double *alpha, double *beta) {
+    const int rb = static_cast<int>((c->n + kPT - 1) / kPT);
+    const int nt = static_cast<int>((c->n + kPN - 1) / kPN);
+    DevBuf b;
+    DOCH_CHECK(b.ensure(sizeof(double) * rb));
+    proc_rowabs<<<rb, kPT>>>(c->n, c->proc_offset, nt, b.as<double>());
+    cudaError_t e = cudaGetLastError();
+    std::vector<double> h(rb);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), b.ptr, sizeof(double) * rb, cudaMemcpyDeviceToHost);
+    b.release();
+    if (e != cudaSuccess) return cuda_fail(e, "proc_rowabs");
+    const double rowmax = *std::max_element(h.begin(), h.end());
+    const double n = static_cast<double>(c->n);
+    const double cnt = n * (n - 1.0);
+    const double mean = c->proc_s1 / cnt;
+    const double var = std::max(0.0, c->proc_s2 / cnt - mean * mean);
+    *alpha = eta * 2.0 * std::sqrt(var) * std::sqrt(n);
+    *beta = std::pow(n, 1.5) * (*alpha + rowmax);
+    return ISING_OK;
+}
+
+}  // namespace doch
