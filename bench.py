@@ -715,8 +715,93 @@ class S5:
         self.N.ising_destroy(self.h)
 
 
+class Proc:
+    """Procedural dense couplings J_ij = sin(i j + 100) of Supplementary Note 9 (the fully connected
+    benchmark matrix, never stored), n = 1e6, one replica, FP32: 10 DOCH steps + sign + energy."""
+
+    dominant = "proc_partial"
+    dtype = "f32"
+    OPS_PER_COUPLING = 13  # phase add 2, fold 2, convert 1, square and scale 2, polynomial 5, sign 1
+
+    def __init__(self, args, rank, N, I, torch):
+        self.n, self.R, self.iters = args.proc_n, 1, args.proc_iters
+        self.N, self.torch = N, torch
+        t0 = time.perf_counter()
+        self.h = N.ising_create_procedural(self.n, 100, flags=N.FLAG_ASYNC)
+        t1 = time.perf_counter()
+        self.alpha, self.beta = N.ising_params_device(self.h, eta=1.0, method=2)
+        t2 = time.perf_counter()
+        self.x0 = I.x0_uniform(self.n, self.R, seed=SEED + 1000 * rank)
+        self.x0_d = torch.from_numpy(self.x0).cuda()
+        self.x = torch.empty_like(self.x0_d)
+        self.E = torch.zeros(self.R, dtype=torch.float64, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        # per DOCH step: products + finish; readout: spins, products, quadratic form
+        self.launches = 2 * self.iters + 3
+        self.config = {"workload": f"procedural dense J_ij = sin(ij + 100), n={self.n} (n^2 = {self.n ** 2:.1e} "
+                                   f"couplings generated per product), R={self.R}, FP32, {self.iters} DOCH steps "
+                                   f"+ sign + FP64 energy",
+                       "n": self.n, "replicas": self.R, "iters": self.iters,
+                       "create_ms": 1e3 * (t1 - t0), "params_ms": 1e3 * (t2 - t1),
+                       "l2": "compute bound; the iterate (4 MB) is L2-resident; no flush",
+                       "alpha_beta": "Wigner estimate on the device, eta = 1, beta of Eq. alphabeta"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_d)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_f64=self.E, stream=sid)
+
+    def roofline(self, per_launch_s):
+        # ALU bound: lane operations per coupling (13 for the coupling, one FMA per replica) against
+        # 152 SMs x 128 FP32/INT32 lanes x 2.07 GHz (the maximum SM clock)
+        ops = float(self.n) ** 2 * (self.OPS_PER_COUPLING + self.R)
+        ach = ops / per_launch_s / 1e9
+        peak = 152 * 128 * 2.07
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant,
+                "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz max SM clock",
+                "algorithmic_ops_per_launch": ops, "couplings_per_s": float(self.n) ** 2 / per_launch_s,
+                "launch": "one coupling product (proc_partial over all column splits + proc_finish_step)"}
+
+    def e2e(self, n_steps, sid):
+        N = self.N
+        xh = self.torch.from_numpy(self.x0.copy()).pin_memory().numpy()
+        Eh = np.zeros(self.R)
+        w0 = time.perf_counter()
+        for _ in range(n_steps):
+            N.ising_iterate(self.h, xh, self.alpha, self.beta, self.iters, stream=sid)
+            N.ising_energy(self.h, xh, E_f64=Eh, stream=sid)
+        dt = time.perf_counter() - w0
+        nb = self.n * self.R * 4
+        return dt, 2 * nb, nb + 8 * self.R, "ising_iterate + ising_energy on pinned host arrays"
+
+    def cpu_baseline(self, args):
+        import oracle as O
+        from paper_2509_01928_gb300 import inputs as I
+        n, iters = 4000, 300
+        J = I.procedural_sin(n, 100)
+        x0 = I.x0_uniform(n, self.R, seed=SEED, dtype=np.float64)
+        a, b = O.alpha_beta(J, eta=1.0, method="wigner")
+        P = O.Problem(J)
+        t0 = time.perf_counter()
+        O.doch(P, x0, a, b, iters)
+        dt = time.perf_counter() - t0
+        return {"value": n * self.R * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"procedural sin(ij + 100) n={n} held as a stored FP64 matrix, R={self.R}, "
+                          f"{iters} FP64 DOCH steps"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
 WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800,
-             "adoch": Adoch, "s5": S5}
+             "adoch": Adoch, "s5": S5, "proc": Proc}
 
 
 def run_ours(args):
@@ -833,7 +918,7 @@ def main():
                     help="torus (default: 10^4 x 10^4 lattice), dense (16384 x 256 on tcgen05), "
                          "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64), "
                          "adoch (Algorithm 2 on the 10^4 x 10^4 lattice), s5 (Algorithm S5 matrix generated on "
-                         "the device, n = 1e5)")
+                         "the device, n = 1e5), proc (procedural dense sin(ij + 100), n = 1e6)")
     ap.add_argument("--dense-n", type=int, default=16384)
     ap.add_argument("--dense-iters", type=int, default=1000)
     ap.add_argument("--batch-count", type=int, default=512)
@@ -842,6 +927,8 @@ def main():
     ap.add_argument("--s5-n", type=int, default=100000)
     ap.add_argument("--s5-p", type=float, default=0.1)
     ap.add_argument("--s5-iters", type=int, default=500)
+    ap.add_argument("--proc-n", type=int, default=1000000)
+    ap.add_argument("--proc-iters", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
