@@ -399,6 +399,8 @@ void destroy_ctx(ising_context *c) {
     c->ckpt.release();
     c->work.release();
     c->batch_items.release();
+    c->proc_units.release();
+    c->proc_acc.release();
     delete c;
 }
 

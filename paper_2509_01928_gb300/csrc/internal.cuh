@@ -95,6 +95,11 @@ struct ising_context {
     // the fly; proc_s1 / proc_s2 = sums of J_ij and J_ij^2 over i != j (FP64)
     int64_t proc_offset = 0;
     double proc_s1 = 0.0, proc_s2 = 0.0;
+    // one-replica symmetric product: work units (int4) and the fixed-point
+    // accumulators (int64 [n], zero between products) plus the max |x| word
+    doch::DevBuf proc_units;
+    int proc_units_count = 0;
+    doch::DevBuf proc_acc;
     // field (both precisions; integer copy when integral)
     float *h_f32 = nullptr;
     double *h_f64 = nullptr;

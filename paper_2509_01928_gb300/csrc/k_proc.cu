@@ -281,6 +281,205 @@ int stream_blocks(const ising_context *c, int64_t count) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 8LL * c->num_sms)));
 }
 
+
+// ---- one replica: each generated coupling serves both J_ij x_j and J_ji x_i ----
+//
+// Row tiles of kSR kPT = 1024 rows (kSR rows per thread, rows r0 + t + 256 k).
+// A tile's own 1024 x 1024 diagonal block runs as rows only (j != i tested);
+// every column j beyond the tile is taken once, in column tiles of 256: the
+// thread adds J_ij x_j to its rows' sums and J_ij x_i to per-lane column sums,
+// which a 32-lane butterfly (each step halves the columns a lane holds) and a
+// fixed-order sum over the 8 warps reduce to one value per column. Rows and
+// columns receive their contributions from many CTAs, so they accumulate as
+// int64 fixed-point numbers (scale 2^k with n max|x| 2^k < 2^61): integer
+// additions commute, so the atomics give the same sums in any order. Each
+// added value is an FP32 sum over at most 256 terms (columns) or 1024 terms
+// (rows of a column), rounded once to the fixed point (relative 2^-61 n).
+
+constexpr int kSR = 4;             // rows per thread
+constexpr int kSTR = kSR * kPT;    // rows per row tile
+constexpr int kSTC = 256;          // columns per column tile
+constexpr int kSUnit = 64;         // column tiles per work unit
+
+// lane l returns the sum over the warp's lanes of v[l] (v[b]: column b of a 32-column chunk)
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const bool up = lane & m;
+#pragma unroll
+        for (int b = 0; b < m; ++b) {
+            const float send = up ? v[b] : v[b + m];
+            const float keep = up ? v[b + m] : v[b];
+            v[b] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    return v[0];
+}
+
+// exponent k of the fixed-point scale 2^k with n m 2^k < 2^60 for m = max |x| (1 for spins)
+__host__ __device__ __forceinline__ int fixed_exp(float m, int64_t n) {
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m * static_cast<float>(n), &e);  // m n < 2^e up to the rounding of the product
+    const int k = 59 - e;
+    return k < -120 ? -120 : (k > 120 ? 120 : k);
+}
+
+__global__ void proc_maxabs(const float *__restrict__ x, int64_t n, unsigned *__restrict__ out) {
+    float m = 0.f;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as integers
+}
+
+template <typename XT, bool DIAG>
+__device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long long *__restrict__ acc, float scale,
+                                         int4 un, int64_t n, int64_t offset) {
+    __shared__ __align__(16) float xs[kSTC];
+    __shared__ float red[kPT / 32][kSTC];
+    const int64_t r0 = static_cast<int64_t>(un.x) * kSTR;
+    const int64_t c_begin = DIAG ? r0 : static_cast<int64_t>(un.y) * kSTC;
+    const int ntile = DIAG ? static_cast<int>((min(n, r0 + kSTR) - r0 + kSTC - 1) / kSTC) : un.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float xr[kSR];
+    uint64_t P[kSR], D[kSR];
+    long long racc[kSR];
+#pragma unroll
+    for (int k = 0; k < kSR; ++k) {
+        const int64_t i = r0 + threadIdx.x + kPT * k;
+        xr[k] = i < n ? static_cast<float>(x[i]) : 0.f;
+        const uint64_t i1 = static_cast<uint64_t>(i) + 1;
+        D[k] = phase64(i1);
+        P[k] = phase64(i1 * (static_cast<uint64_t>(c_begin) + 1) + static_cast<uint64_t>(offset));
+        racc[k] = 0;
+    }
+    for (int tile = 0; tile < ntile; ++tile) {
+        const int64_t c0 = c_begin + static_cast<int64_t>(tile) * kSTC;
+        __syncthreads();
+        xs[threadIdx.x] = c0 + threadIdx.x < n ? static_cast<float>(x[c0 + threadIdx.x]) : 0.f;
+        __syncthreads();
+        float trs[kSR];
+#pragma unroll
+        for (int k = 0; k < kSR; ++k) trs[k] = 0.f;
+        for (int chunk = 0; chunk < kSTC / 32; ++chunk) {
+            float col[32], crs[kSR];
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) crs[k] = 0.f;
+#pragma unroll
+            for (int b4 = 0; b4 < 32; b4 += 4) {
+                const float4 xq = *reinterpret_cast<const float4 *>(xs + chunk * 32 + b4);
+                const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int b = b4 + bb;
+#pragma unroll
+                    for (int k = 0; k < kSR; ++k) {
+                        float w = coupling(P[k]);
+                        P[k] += D[k];
+                        if (DIAG && c0 + chunk * 32 + b == r0 + threadIdx.x + kPT * k) w = 0.f;
+                        crs[k] = fmaf(w, xv[bb], crs[k]);
+                        if (!DIAG) col[b] = k == 0 ? w * xr[0] : fmaf(w, xr[k], col[b]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) trs[k] += crs[k];
+            if (!DIAG) red[warp][chunk * 32 + lane] = reduce_scatter32(col);
+        }
+#pragma unroll
+        for (int k = 0; k < kSR; ++k) racc[k] += __float2ll_rn(trs[k] * scale);
+        if (!DIAG) {
+            __syncthreads();
+            float cs = 0.f;
+#pragma unroll
+            for (int w = 0; w < kPT / 32; ++w) cs += red[w][threadIdx.x];
+            if (c0 + threadIdx.x < n)
+                atomicAdd(acc + c0 + threadIdx.x, static_cast<unsigned long long>(__float2ll_rn(cs * scale)));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kSR; ++k) {
+        const int64_t i = r0 + threadIdx.x + kPT * k;
+        if (i < n) atomicAdd(acc + i, static_cast<unsigned long long>(racc[k]));
+    }
+}
+
+// unit: (row tile, first column tile, column tiles, 1 = diagonal block); m > 0: fixed max |x|
+template <typename XT>
+__global__ void __launch_bounds__(kPT, 2)
+proc_sym(const XT *__restrict__ x, unsigned long long *__restrict__ acc, const unsigned *__restrict__ maxbits,
+         float m, const int4 *__restrict__ units, int64_t n, int64_t offset) {
+    const int4 un = units[blockIdx.x];
+    const float scale = ldexpf(1.f, fixed_exp(m > 0.f ? m : __uint_as_float(*maxbits), n));
+    if (un.w) sym_unit<XT, true>(x, acc, scale, un, n, offset);
+    else sym_unit<XT, false>(x, acc, scale, un, n, offset);
+}
+
+// x_out = cbrt((u + alpha x) / beta) with u the fixed-point sums; clears them
+__global__ void proc_sym_finish(unsigned long long *__restrict__ acc, const unsigned *__restrict__ maxbits,
+                                const float *__restrict__ x, float *__restrict__ xo, int64_t n, float alpha,
+                                float zs, float xsc) {
+    const double inv = ldexp(1.0, -fixed_exp(__uint_as_float(*maxbits), n));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float u = static_cast<float>(static_cast<double>(static_cast<long long>(acc[i])) * inv);
+        acc[i] = 0ull;
+        xo[i] = cbrt_pow2((u + alpha * x[i]) * zs) * xsc;
+    }
+}
+
+// qpart[block] = sum over the block's rows of s_i u_i (FP64, fixed order); clears the sums
+__global__ void __launch_bounds__(kQT)
+proc_sym_quad(unsigned long long *__restrict__ acc, const int8_t *__restrict__ s, int64_t n, double inv,
+              double *__restrict__ qpart) {
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = static_cast<int64_t>(blockIdx.x) * rows_per, hi = min(n, lo + rows_per);
+    double q = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kQT) {
+        q += static_cast<double>(s[i]) * (static_cast<double>(static_cast<long long>(acc[i])) * inv);
+        acc[i] = 0ull;
+    }
+    __shared__ double red[kQT];
+    red[threadIdx.x] = q;
+    __syncthreads();
+    for (int w = kQT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) qpart[blockIdx.x] = red[0];
+}
+
+// work units of the symmetric product (diagonal blocks first), and the
+// accumulators [n] int64 + the max |x| word, zeroed once
+ising_status_t sym_setup(ising_context *c) {
+    if (c->proc_units_count > 0) return ISING_OK;
+    const int64_t n = c->n;
+    const int64_t rt = (n + kSTR - 1) / kSTR, ct = (n + kSTC - 1) / kSTC;
+    std::vector<int4> u;
+    for (int64_t I = 0; I < rt; ++I) u.push_back(make_int4(static_cast<int>(I), 0, 0, 1));
+    for (int64_t I = 0; I < rt; ++I) {
+        const int64_t first = (I + 1) * (kSTR / kSTC);
+        for (int64_t t = first; t < ct; t += kSUnit)
+            u.push_back(make_int4(static_cast<int>(I), static_cast<int>(t),
+                                  static_cast<int>(std::min<int64_t>(kSUnit, ct - t)), 0));
+    }
+    if (u.size() > 0x7FFFFFFFu) return fail(ISING_ERR_UNSUPPORTED, "procedural product: too many work units");
+    DOCH_CHECK(c->proc_units.ensure(sizeof(int4) * u.size()));
+    DOCH_CUDA(cudaMemcpy(c->proc_units.ptr, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice));
+    DOCH_CHECK(c->proc_acc.ensure(sizeof(unsigned long long) * n + 256));
+    DOCH_CUDA(cudaMemset(c->proc_acc.ptr, 0, sizeof(unsigned long long) * n + 256));
+    c->proc_units_count = static_cast<int>(u.size());
+    return ISING_OK;
+}
+
+unsigned *sym_maxword(ising_context *c) {
+    return reinterpret_cast<unsigned *>(c->proc_acc.as<unsigned long long>() + c->n);
+}
+
 // m/2 radians for an integer m < 2^64, reduced to [-pi, pi): the turn
 // fraction m / (4 pi) from floor(2^96 / (4 pi)) in integers
 double half_angle(uint64_t m) {
@@ -322,14 +521,26 @@ void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2) {
 
 ising_status_t proc_step(ising_context *c, const float *x_in, float *x_out, int R, double alpha, double inv_beta,
                          cudaStream_t st) {
+    const int k = cbrt_prescale_exp(inv_beta);
+    const float zs = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+    const float xsc = std::ldexp(1.0f, -k);
+    if (R == 1) {
+        DOCH_CHECK(sym_setup(c));
+        unsigned *mw = sym_maxword(c);
+        DOCH_CUDA(cudaMemsetAsync(mw, 0, sizeof(unsigned), st));
+        proc_maxabs<<<stream_blocks(c, c->n), 256, 0, st>>>(x_in, c->n, mw);
+        proc_sym<float><<<c->proc_units_count, kPT, 0, st>>>(x_in, c->proc_acc.as<unsigned long long>(), mw, 0.f,
+                                                           c->proc_units.as<int4>(), c->n, c->proc_offset);
+        proc_sym_finish<<<stream_blocks(c, c->n), 256, 0, st>>>(c->proc_acc.as<unsigned long long>(), mw, x_in,
+                                                              x_out, c->n, static_cast<float>(alpha), zs, xsc);
+        DOCH_CUDA(cudaGetLastError());
+        return ISING_OK;
+    }
     const SplitPlan pl = plan_splits(c);
     const int64_t count = c->n * R;
     DOCH_CHECK(c->partials.ensure(sizeof(float) * count * pl.S));
     float *part = c->partials.as<float>();
     DOCH_CHECK(proc_products<float>(c, x_in, part, R, pl, st));
-    const int k = cbrt_prescale_exp(inv_beta);
-    const float zs = static_cast<float>(std::ldexp(inv_beta, 3 * k));
-    const float xsc = std::ldexp(1.0f, -k);
     proc_finish_step<<<stream_blocks(c, count), 256, 0, st>>>(part, pl.S, x_in, x_out, count,
                                                              static_cast<float>(alpha), zs, xsc);
     DOCH_CUDA(cudaGetLastError());
@@ -350,8 +561,16 @@ ising_status_t proc_energy(ising_context *c, const void *x, int xtype, int R, do
     int8_t *s = reinterpret_cast<int8_t *>(c->partials.as<unsigned char>() + part_b);
     double *qp = reinterpret_cast<double *>(c->partials.as<unsigned char>() + part_b + spin_b);
     DOCH_CHECK(write_spins(c, x, xtype, R, s, st));
-    DOCH_CHECK(proc_products<int8_t>(c, s, part, R, pl, st));
-    proc_finish_quad<<<dim3(qb, R), kQT, 0, st>>>(part, pl.S, s, c->n, R, qp);
+    if (R == 1) {
+        DOCH_CHECK(sym_setup(c));
+        proc_sym<int8_t><<<c->proc_units_count, kPT, 0, st>>>(s, c->proc_acc.as<unsigned long long>(), nullptr, 1.f,
+                                                            c->proc_units.as<int4>(), c->n, c->proc_offset);
+        const double inv = std::ldexp(1.0, -fixed_exp(1.f, c->n));
+        proc_sym_quad<<<qb, kQT, 0, st>>>(c->proc_acc.as<unsigned long long>(), s, c->n, inv, qp);
+    } else {
+        DOCH_CHECK(proc_products<int8_t>(c, s, part, R, pl, st));
+        proc_finish_quad<<<dim3(qb, R), kQT, 0, st>>>(part, pl.S, s, c->n, R, qp);
+    }
     DOCH_CUDA(cudaGetLastError());
     std::vector<double> qh(static_cast<size_t>(R) * qb);
     DOCH_CUDA(cudaMemcpyAsync(qh.data(), qp, sizeof(double) * qh.size(), cudaMemcpyDeviceToHost, st));

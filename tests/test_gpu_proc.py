@@ -10,8 +10,11 @@ when J is merely rounded to FP32), so whole trajectories are compared at the
 FP32 tolerance of 1e-5 over the first three steps only, and every later step
 is checked by replay: the oracle applies T to the device's own iterate x^(k)
 and the device's x^(k+1) must agree with it to 1e-5 (relative, per replica).
-Energies are compared at 1e-6 relative, alpha (closed-form sums in FP64) at
-1e-9 and beta (device row sums of |J_ij|) at 1e-5.
+Energies are compared at 1e-6 of n^1.5 (the energy scale of low-energy
+states), alpha (closed-form sums in FP64) at 1e-9 and beta (device row sums
+of |J_ij|) at 1e-5. One replica takes the symmetric product (each coupling
+generated once for J_ij x_j and J_ji x_i, fixed-point accumulation), wider
+replica groups the row product; both are covered.
 """
 import numpy as np
 import pytest
@@ -54,7 +57,8 @@ def _replay(hd, J, x0, alphas, beta):
     return xs
 
 
-@pytest.mark.parametrize("n,R,iters", [(1000, 1, 20), (2048, 3, 12), (3001, 16, 8), (777, 20, 10), (2, 2, 5)])
+@pytest.mark.parametrize("n,R,iters", [(1000, 1, 20), (5000, 1, 6), (4097, 1, 4), (2048, 3, 12), (3001, 16, 8),
+                                       (777, 20, 10), (2, 2, 5), (2, 1, 3)])
 def test_proc_doch_matches_oracle(n, R, iters):
     J = I.procedural_sin(n, C)
     alpha, beta = O.alpha_beta(J, eta=1.0, method="wigner" if n > 2 else "eig")
@@ -93,7 +97,7 @@ def test_proc_schedule_matches_oracle():
         N.ising_destroy(hd)
 
 
-@pytest.mark.parametrize("n,R", [(1000, 5), (2560, 1), (300, 17)])
+@pytest.mark.parametrize("n,R", [(1000, 5), (2560, 1), (4097, 1), (300, 17)])
 def test_proc_energy_matches_oracle(n, R):
     J = I.procedural_sin(n, C)
     rng = np.random.default_rng(440 + n)
@@ -106,8 +110,11 @@ def test_proc_energy_matches_oracle(n, R):
         Ed, Cd, best = np.zeros(R), np.zeros(R), np.zeros(1, np.int32)
         sd = np.zeros((n, R), np.int8)
         N.ising_energy(hd, torch.from_numpy(x).cuda(), E_f64=Ed, cut_f64=Cd, best=best, spins=sd)
-        assert np.all(np.abs(Ed - E) <= 1e-6 * np.abs(E).max())
-        assert np.all(np.abs(Cd - cut) <= 1e-6 * np.abs(cut).max())
+        # relative to the energy scale of the problem (|E| ~ 0.5 n^1.5 for low-energy states;
+        # random spins as here sit near E ~ n, where the FP32 sums' absolute error dominates)
+        scale = n ** 1.5
+        assert np.all(np.abs(Ed - E) <= 1e-6 * scale)
+        assert np.all(np.abs(Cd - cut) <= 1e-6 * scale)
         assert np.array_equal(sd, s)
         assert best[0] == int(np.argmin(Ed))
         # I8 spins give the same numbers
