@@ -719,9 +719,11 @@ class Proc:
     """Procedural dense couplings J_ij = sin(i j + 100) of Supplementary Note 9 (the fully connected
     benchmark matrix, never stored), n = 1e6, one replica, FP32: 10 DOCH steps + sign + energy."""
 
-    dominant = "proc_partial"
+    dominant = "proc_sym"
     dtype = "f32"
     OPS_PER_COUPLING = 13  # phase add 2, fold 2, convert 1, square and scale 2, polynomial 5, sign 1
+    # one replica: the symmetric product generates each unordered pair once (13 / 2 per coupling)
+    # and multiply-adds it twice; wider replica groups generate every coupling (13 per coupling)
 
     def __init__(self, args, rank, N, I, torch):
         self.n, self.R, self.iters = args.proc_n, 1, args.proc_iters
@@ -737,8 +739,8 @@ class Proc:
         self.E = torch.zeros(self.R, dtype=torch.float64, device="cuda")
         self.units = float(self.n) * self.R * self.iters
         self.dominant_launches = self.iters
-        # per DOCH step: products + finish; readout: spins, products, quadratic form
-        self.launches = 2 * self.iters + 3
+        # per DOCH step: max |x|, symmetric product, finish; readout: spins, product, quadratic form
+        self.launches = 3 * self.iters + 3
         self.config = {"workload": f"procedural dense J_ij = sin(ij + 100), n={self.n} (n^2 = {self.n ** 2:.1e} "
                                    f"couplings generated per product), R={self.R}, FP32, {self.iters} DOCH steps "
                                    f"+ sign + FP64 energy",
@@ -758,16 +760,17 @@ class Proc:
         N.ising_energy(self.h, self.x, E_f64=self.E, stream=sid)
 
     def roofline(self, per_launch_s):
-        # ALU bound: lane operations per coupling (13 for the coupling, one FMA per replica) against
+        # ALU bound: lane operations per coupling (generation + one FMA per replica) against
         # 152 SMs x 128 FP32/INT32 lanes x 2.07 GHz (the maximum SM clock)
-        ops = float(self.n) ** 2 * (self.OPS_PER_COUPLING + self.R)
+        gen = self.OPS_PER_COUPLING / 2 if self.R == 1 else self.OPS_PER_COUPLING
+        ops = float(self.n) ** 2 * (gen + self.R)
         ach = ops / per_launch_s / 1e9
         peak = 152 * 128 * 2.07
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
                 "traffic": None, "kernel": self.dominant,
                 "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz max SM clock",
                 "algorithmic_ops_per_launch": ops, "couplings_per_s": float(self.n) ** 2 / per_launch_s,
-                "launch": "one coupling product (proc_partial over all column splits + proc_finish_step)"}
+                "launch": "one coupling product (proc_maxabs + proc_sym over all work units + proc_sym_finish)"}
 
     def e2e(self, n_steps, sid):
         N = self.N

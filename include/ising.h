@@ -173,8 +173,10 @@ ISING_API ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int
  * the paper's 10^6- and 10^7-spin fully connected runs): J_ij = sin(i j + c)
  * for 1-based indices i != j, J_ii = 0, no field. Nothing of J is stored: the
  * kernels generate every coupling where it is used (Algorithm S6's blocks, on
- * one GPU), n^2 sines per coupling product, from an exact integer phase and
- * the hardware sine (each coupling within about 1e-6 of the exact value).
+ * one GPU) from an exact integer phase and a minimax polynomial (each FP32
+ * coupling within 3.3e-7 of the exact value, rms 6e-8): n^2 / 2 couplings per
+ * product for one replica (each serves J_ij x_j and J_ji x_i; order-independent
+ * int64 fixed-point sums), n^2 for more.
  *   n       2 .. 2^30 spins;  c  0 .. 2^40 (the paper uses 100).
  * The handle supports ising_iterate (F32 iterates, no H_trace),
  * ising_iterate_until (F32), ising_energy (E_f64, cut_f64, best, spins; the

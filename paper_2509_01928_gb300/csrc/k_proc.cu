@@ -8,13 +8,16 @@
 // column j + 1 is that of column j plus (i F) mod 2^96; the kernels keep the top
 // 64 bits of both (the truncation adds at most one 2^-64 turn per column) and
 // advance four columns at a time on four independent chains.
-// Coupling. With s the top 32 bits of the phase as a signed integer, the
-// angle is pi y for y = s / 2^31 in [-1, 1), and sin(pi y) = sign(y)
-// cos(pi (|y| - 1/2)) with pi (|y| - 1/2) in [-pi/2, pi/2]; the cosine is an
-// even polynomial of degree 10 in that argument whose coefficients minimise
-// the largest absolute error on the interval (Remez exchange; 2.2e-10 before
-// rounding). Measured against the FP64 sine of the exact phase, the FP32
-// couplings are within 1.7e-7 (rms 3.0e-8), about the rounding of J to FP32.
+// Coupling. Between resynchronisations from the 64-bit phase (every 32
+// columns) a column's top 32 bits advance by the rounded top 32 bits of the
+// increment (at most 16 units of 2^-32 turn of drift). With s those bits as a
+// signed integer, the angle is pi y for y = s / 2^31 in [-1, 1), and
+// sin(pi y) = sign(y) cos(pi (|y| - 1/2)) with pi (|y| - 1/2) in
+// [-pi/2, pi/2]; the cosine is an even polynomial of degree 8 whose
+// coefficients minimise the largest absolute error on the interval (Remez
+// exchange). Measured against the FP64 sine of the exact phase, the FP32
+// couplings are within 3.3e-7 (rms 6.0e-8), about one FP32 unit in the last
+// place of a coupling of size 1/2 to 1.
 // Product. One thread per row, CTAs of kPT rows, the columns in tiles of kPN
 // staged in shared memory (each value read by all threads: a broadcast);
 // per-tile sums, then a sum over the tiles of a column split. The splits
@@ -52,22 +55,32 @@ __host__ __device__ __forceinline__ uint64_t phase64(uint64_t a) {
     return mulmod96_top(a, 0x28BE60DBu, 0x9391054Au, 0x7F09D5F4u);
 }
 
-// J for the phase p: sin(pi y) = sign(y) cos(pi (|y| - 1/2)), y = s / 2^31
-__device__ __forceinline__ float coupling(uint64_t p) {
-    const int32_t s = static_cast<int32_t>(p >> 32);
-    const float v = static_cast<float>(abs(s) - 0x40000000);  // (|y| - 1/2) 2^31 (|INT_MIN| wraps to the same angle)
-    const float u = v * v * 2.1401293066467156e-18f;          // (pi (|y| - 1/2))^2
-    float q = -2.6051495269991556e-07f;
-    q = fmaf(q, u, 2.476016135530425e-05f);
-    q = fmaf(q, u, -0.001388836140031622f);
-    q = fmaf(q, u, 0.04166663625807217f);
-    q = fmaf(q, u, -0.499999993584718f);
-    q = fmaf(q, u, 0.999999999780652f);
-    return __uint_as_float(__float_as_uint(q) ^ (static_cast<uint32_t>(s) & 0x80000000u));
+// J for the top 32 bits t of the phase: with s = (int32) t and y = s / 2^31,
+// sin(pi y) = sign(y) cos(pi (|y| - 1/2)); the argument pi |y| - pi/2 is one
+// multiply-add from the float of |s| (whose rounding, and that of the two
+// constants, moves it by at most 2.4e-7 where |y| is near 1 and sin(pi y) is
+// near 0), the cosine a minimax even polynomial of degree 8 (4.7e-8 before
+// rounding)
+__device__ __forceinline__ float coupling(uint32_t t) {
+    const float a = static_cast<float>(abs(static_cast<int32_t>(t)));  // |INT_MIN| wraps to the same angle
+    const float x = fmaf(a, 1.4629180792671596e-09f, -1.5707963267948966f);
+    const float u = x * x;
+    float q = 2.3153931635876185e-05f;
+    q = fmaf(q, u, -0.0013853704307259674f);
+    q = fmaf(q, u, 0.041663584693001555f);
+    q = fmaf(q, u, -0.49999905347077034f);
+    q = fmaf(q, u, 0.9999999534666968f);
+    return __uint_as_float(__float_as_uint(q) ^ (t & 0x80000000u));
+}
+
+// the top 32 bits of a phase increment, rounded
+__device__ __forceinline__ uint32_t top32_rounded(uint64_t d) {
+    return static_cast<uint32_t>((d + 0x80000000ull) >> 32);
 }
 
 // One kPN-column tile for RC replicas: tacc[r] = sum_j J_ij x_jr. P[4] are
-// the phases of the next four columns, advanced by D4 = 4 D per group. For
+// the phases of the next four columns (64-bit, advanced by D4 = 4 D per group
+// and resynchronised into 32-bit chains every 8 groups). For
 // RC <= 2 each of the four column chains has its own sums (64 terms each,
 // added pairwise at the end), which shortens the FP32 summation; wider
 // replica groups sum the tile in one chain per replica.
@@ -80,39 +93,48 @@ __device__ __forceinline__ void tile_pass(const float *__restrict__ tf, uint64_t
     for (int k = 0; k < kCh; ++k)
 #pragma unroll
         for (int r = 0; r < RC; ++r) ch[k][r] = 0.f;
-#pragma unroll 2
-    for (int jj = 0; jj < kPN; jj += 4) {
-        float w[4];
+    const uint32_t d4 = top32_rounded(D4);
+    for (int j8 = 0; j8 < kPN; j8 += 32) {
+        uint32_t t[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            w[u] = coupling(P[u]);
-            P[u] += D4;
-            if (DIAG && jj + u == diag_col) w[u] = 0.f;
+            t[u] = static_cast<uint32_t>(P[u] >> 32);
+            P[u] += 8 * D4;
         }
-        if constexpr (RC < 4) {
-            float v[4 * RC];
 #pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                const float4 g = reinterpret_cast<const float4 *>(tf + jj * RC)[q];
-                v[4 * q] = g.x;
-                v[4 * q + 1] = g.y;
-                v[4 * q + 2] = g.z;
-                v[4 * q + 3] = g.w;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int r = 0; r < RC; ++r) ch[u % kCh][r] = fmaf(w[u], v[u * RC + r], ch[u % kCh][r]);
-        } else {
+        for (int jj = j8; jj < j8 + 32; jj += 4) {
+            float w[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
+                w[u] = coupling(t[u]);
+                t[u] += d4;
+                if (DIAG && jj + u == diag_col) w[u] = 0.f;
+            }
+            if constexpr (RC < 4) {
+                float v[4 * RC];
 #pragma unroll
-                for (int q = 0; q < RC / 4; ++q) {
-                    const float4 g = reinterpret_cast<const float4 *>(tf + (jj + u) * RC)[q];
-                    ch[0][4 * q] = fmaf(w[u], g.x, ch[0][4 * q]);
-                    ch[0][4 * q + 1] = fmaf(w[u], g.y, ch[0][4 * q + 1]);
-                    ch[0][4 * q + 2] = fmaf(w[u], g.z, ch[0][4 * q + 2]);
-                    ch[0][4 * q + 3] = fmaf(w[u], g.w, ch[0][4 * q + 3]);
+                for (int q = 0; q < RC; ++q) {
+                    const float4 g = reinterpret_cast<const float4 *>(tf + jj * RC)[q];
+                    v[4 * q] = g.x;
+                    v[4 * q + 1] = g.y;
+                    v[4 * q + 2] = g.z;
+                    v[4 * q + 3] = g.w;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) ch[u % kCh][r] = fmaf(w[u], v[u * RC + r], ch[u % kCh][r]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int q = 0; q < RC / 4; ++q) {
+                        const float4 g = reinterpret_cast<const float4 *>(tf + (jj + u) * RC)[q];
+                        ch[0][4 * q] = fmaf(w[u], g.x, ch[0][4 * q]);
+                        ch[0][4 * q + 1] = fmaf(w[u], g.y, ch[0][4 * q + 1]);
+                        ch[0][4 * q + 2] = fmaf(w[u], g.z, ch[0][4 * q + 2]);
+                        ch[0][4 * q + 3] = fmaf(w[u], g.w, ch[0][4 * q + 3]);
+                    }
                 }
             }
         }
@@ -223,7 +245,7 @@ proc_rowabs(int64_t n, int64_t offset, int n_tiles, double *__restrict__ bmax) {
         const int cols = n - j0 < kPN ? static_cast<int>(n - j0) : kPN;
         float ta = 0.f;
         for (int jj = 0; jj < cols; ++jj) {
-            const float w = fabsf(coupling(P));
+            const float w = fabsf(coupling(static_cast<uint32_t>(P >> 32)));
             P += D;
             ta += (j0 + jj == i) ? 0.f : w;
         }
@@ -346,14 +368,17 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
     const int ntile = DIAG ? static_cast<int>((min(n, r0 + kSTR) - r0 + kSTC - 1) / kSTC) : un.z;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float xr[kSR];
-    uint64_t P[kSR], D[kSR];
+    uint64_t P[kSR], D32[kSR];  // phase at the next 32-column chunk, its advance per chunk
+    uint32_t d[kSR];            // rounded top 32 bits of the per-column increment
     long long racc[kSR];
 #pragma unroll
     for (int k = 0; k < kSR; ++k) {
         const int64_t i = r0 + threadIdx.x + kPT * k;
         xr[k] = i < n ? static_cast<float>(x[i]) : 0.f;
         const uint64_t i1 = static_cast<uint64_t>(i) + 1;
-        D[k] = phase64(i1);
+        const uint64_t D = phase64(i1);
+        D32[k] = 32 * D;
+        d[k] = top32_rounded(D);
         P[k] = phase64(i1 * (static_cast<uint64_t>(c_begin) + 1) + static_cast<uint64_t>(offset));
         racc[k] = 0;
     }
@@ -367,8 +392,13 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
         for (int k = 0; k < kSR; ++k) trs[k] = 0.f;
         for (int chunk = 0; chunk < kSTC / 32; ++chunk) {
             float col[32], crs[kSR];
+            uint32_t tk[kSR];
 #pragma unroll
-            for (int k = 0; k < kSR; ++k) crs[k] = 0.f;
+            for (int k = 0; k < kSR; ++k) {
+                crs[k] = 0.f;
+                tk[k] = static_cast<uint32_t>(P[k] >> 32);
+                P[k] += D32[k];
+            }
 #pragma unroll
             for (int b4 = 0; b4 < 32; b4 += 4) {
                 const float4 xq = *reinterpret_cast<const float4 *>(xs + chunk * 32 + b4);
@@ -378,8 +408,8 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
                     const int b = b4 + bb;
 #pragma unroll
                     for (int k = 0; k < kSR; ++k) {
-                        float w = coupling(P[k]);
-                        P[k] += D[k];
+                        float w = coupling(tk[k]);
+                        tk[k] += d[k];
                         if (DIAG && c0 + chunk * 32 + b == r0 + threadIdx.x + kPT * k) w = 0.f;
                         crs[k] = fmaf(w, xv[bb], crs[k]);
                         if (!DIAG) col[b] = k == 0 ? w * xr[0] : fmaf(w, xr[k], col[b]);

@@ -2,7 +2,7 @@
 device against the FP64 oracle.
 
 The device generates every coupling in FP32 from an exact integer phase
-(within 1.7e-7 of sin(i j + c), rms 3e-8) and sums the n products of a row in
+(within 3.3e-7 of sin(i j + c), rms 6e-8) and sums the n products of a row in
 FP32, so one step of Eq. FPE carries a relative error of a few 1e-7. On these
 fully connected matrices the first tens of DOCH steps amplify any such error
 by up to about 100 (the oracle's own trajectory moves by 1e-5 to 3e-5 there
