@@ -721,9 +721,9 @@ class Proc:
 
     dominant = "proc_sym"
     dtype = "f32"
-    OPS_PER_COUPLING = 13  # phase add 2, fold 2, convert 1, square and scale 2, polynomial 5, sign 1
-    # one replica: the symmetric product generates each unordered pair once (13 / 2 per coupling)
-    # and multiply-adds it twice; wider replica groups generate every coupling (13 per coupling)
+    OPS_PER_COUPLING = 10  # phase add 1, |s| 1, convert 1, fold 1, square 1, polynomial 4, sign 1
+    # one replica: the symmetric product generates each unordered pair once (10 / 2 per coupling)
+    # and multiply-adds it twice; wider replica groups generate every coupling (10 per coupling)
 
     def __init__(self, args, rank, N, I, torch):
         self.n, self.R, self.iters = args.proc_n, 1, args.proc_iters
