@@ -370,6 +370,18 @@ ISING_API ising_status_t ising_energy_torus_noalloc(const int8_t *right, const i
 ISING_API ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
                                              int32_t k, void *stream);
 
+/*
+ * Diagnostic: the procedural couplings J_ij = sin(i j + c) (1-based i, j;
+ * J_ii = 0) for rows row0 .. row0 + rows - 1 and columns col0 .. col0 + cols - 1
+ * (0-based indices), evaluated on the device exactly as the product kernels of
+ * an ising_create_procedural handle generate them (64-bit phase every 32nd
+ * column from col0, 32-bit increments in between), into J_out [rows][cols]
+ * FP32 (device array). Indices below 2^30, c in 0 .. 2^40. Synchronises the
+ * stream.
+ */
+ISING_API ising_status_t ising_selftest_procedural(int64_t row0, int32_t rows, int64_t col0, int32_t cols,
+                                                   int64_t c, float *J_out, void *stream);
+
 /* Static description of a status code. */
 ISING_API const char *ising_status_string(ising_status_t s);
 

@@ -88,6 +88,9 @@ def load():
     lib.ising_energy_torus_noalloc.restype = ctypes.c_int
     lib.ising_selftest_cbrt.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]
     lib.ising_selftest_cbrt.restype = ctypes.c_int
+    lib.ising_selftest_procedural.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int64, _vp, _vp]
+    lib.ising_selftest_procedural.restype = ctypes.c_int
     lib.ising_status_string.argtypes = [ctypes.c_int]
     lib.ising_status_string.restype = ctypes.c_char_p
     lib.ising_last_error.argtypes = []
@@ -293,6 +296,13 @@ def ising_create_procedural(n: int, c: int = 100, flags: int = 0) -> int:
     out = ctypes.c_void_p()
     _check(load().ising_create_procedural(int(n), int(c), int(flags), ctypes.byref(out)), "ising_create_procedural")
     return out.value
+
+
+def ising_selftest_procedural(row0: int, rows: int, col0: int, cols: int, c: int, out, stream=None):
+    """Device couplings sin(i j + c) of a block of rows and columns, generated as the product kernels
+    generate them, into out ([rows][cols] FP32 on the device)."""
+    _check(load().ising_selftest_procedural(int(row0), int(rows), int(col0), int(cols), int(c), _ptr(out),
+                                            _stream(stream, out)), "ising_selftest_procedural")
 
 
 def ising_params_device(handle: int, eta: float = 1.0, method: int = 0):

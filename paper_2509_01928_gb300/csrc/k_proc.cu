@@ -261,6 +261,27 @@ proc_rowabs(int64_t n, int64_t offset, int n_tiles, double *__restrict__ bmax) {
     if (threadIdx.x == 0) bmax[blockIdx.x] = red[0];
 }
 
+// the couplings of rows row0.. and columns col0.. as the product kernels generate
+// them (64-bit phase at every 32nd column, 32-bit chain in between)
+__global__ void proc_couplings(int64_t row0, int rows, int64_t col0, int cols, int64_t offset,
+                               float *__restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const uint64_t i1 = static_cast<uint64_t>(row0 + r) + 1;
+    const uint64_t D = phase64(i1);
+    const uint32_t d = top32_rounded(D);
+    uint64_t P = phase64(i1 * (static_cast<uint64_t>(col0) + 1) + static_cast<uint64_t>(offset));
+    uint32_t t = 0;
+    for (int j = 0; j < cols; ++j) {
+        if ((j & 31) == 0) {
+            t = static_cast<uint32_t>(P >> 32);
+            P += 32 * D;
+        }
+        out[static_cast<int64_t>(r) * cols + j] = row0 + r == col0 + j ? 0.f : coupling(t);
+        t += d;
+    }
+}
+
 struct SplitPlan {
     int row_blocks, n_tiles, tiles_per_split, S;
 };
@@ -641,3 +662,17 @@ ising_status_t proc_params(const ising_context *c, double eta, double *alpha, do
 }
 
 }  // namespace doch
+
+extern "C" ising_status_t ising_selftest_procedural(int64_t row0, int32_t rows, int64_t col0, int32_t cols,
+                                                    int64_t c, float *J_out, void *stream) {
+    using namespace doch;
+    if (!J_out || row0 < 0 || col0 < 0 || rows < 0 || cols < 0 || c < 0 || c > (int64_t(1) << 40) ||
+        row0 + rows > (int64_t(1) << 30) || col0 + cols > (int64_t(1) << 30))
+        return fail(ISING_ERR_INVALID_ARG, "selftest_procedural: bad argument");
+    if (rows == 0 || cols == 0) return ISING_OK;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    proc_couplings<<<(rows + 127) / 128, 128, 0, st>>>(row0, rows, col0, cols, c, J_out);
+    DOCH_CUDA(cudaGetLastError());
+    DOCH_CUDA(cudaStreamSynchronize(st));
+    return ISING_OK;
+}

@@ -215,6 +215,23 @@ def test_proc_full_size_sampled_rows():
     assert _rel(x1[rows], ref).max() <= 1e-5
 
 
+@pytest.mark.parametrize("row0,rows,col0,cols", [(0, 64, 0, 4096), (999_000, 64, 0, 20_000),
+                                                (123_456, 40, 876_000, 3000), (700, 30, 690, 50)])
+def test_proc_couplings_against_the_fp64_sine(row0, rows, col0, cols):
+    """The device couplings (as the product kernels generate them: 64-bit phase every 32nd column,
+    32-bit increments between) against sin(i j + c) in FP64 (i j + c exact below 2^53)."""
+    out = torch.empty((rows, cols), dtype=torch.float32, device="cuda")
+    N.ising_selftest_procedural(row0, rows, col0, cols, C, out)
+    i = np.arange(row0 + 1, row0 + rows + 1, dtype=np.float64)[:, None]
+    j = np.arange(col0 + 1, col0 + cols + 1, dtype=np.float64)[None, :]
+    ref = np.sin(i * j + C)
+    ref[i == j] = 0.0
+    err = out.cpu().numpy().astype(np.float64) - ref
+    assert np.abs(err).max() <= 4e-7
+    assert np.sqrt(np.mean(err * err)) <= 1e-7
+    assert np.all(out.cpu().numpy()[i == j] == 0.0)
+
+
 def test_proc_rejects():
     with pytest.raises(N.IsingError):
         N.ising_create_procedural(1, C)
