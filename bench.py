@@ -558,7 +558,7 @@ class Er800:
 class Adoch:
     """ADOCH (Algorithm 2) on the 10^4 x 10^4 lattice, FP32, R = 1, q = 5, 100 steps per timed step."""
 
-    dominant = "adoch step (adoch_pass + adoch_decide + adoch_update)"
+    dominant = "adoch step (adoch_lattice<false> + adoch_decide + adoch_lattice<true>)"
     dtype = "f32"
 
     def __init__(self, args, rank, N, I, torch):
@@ -596,9 +596,9 @@ class Adoch:
 
     def roofline(self, per_launch_s):
         peak, kind = measured_peaks()
-        # per step and site: pass reads x^k, x^(k-1), u^(k-1) and the couplings, writes u^k
-        # (4 + 4 + 4 + 2 + 4 B); update reads x^k, x^(k-1), u^k, u^(k-1), writes x^(k+1) (20 B)
-        alg = 38 * self.n
+        # per step and site: the pass reads x^k, x^(k-1) and the couplings (10 B); the update reads
+        # them again and writes x^(k+1) (14 B); both coupling products are recomputed, not stored
+        alg = 24 * self.n
         ach = alg / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "kernel": self.dominant, "peak_kind": kind,

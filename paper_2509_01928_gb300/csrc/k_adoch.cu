@@ -21,6 +21,7 @@
 #include <cmath>
 #include <utility>
 
+#include "cbrt.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -230,6 +231,252 @@ int adoch_chunks(const ising_context *c, int R) {
     return static_cast<int>(ch);
 }
 
+// ---- lattice fast path (R = 1, FP32, l_cols % 4 == 0, 16-byte aligned) ----
+//
+// Neither u^k nor u^{k-1} is stored: both passes recompute J x^k and
+// J x^{k-1} from the two iterates (4 + 4 B per site) and the couplings (2 B),
+// so a step reads 10 B per site twice and writes x^{k+1} once (24 B instead of
+// 38 with the stored products). Layout as the DOCH lattice kernel: a CTA of
+// 256 threads owns 1024 columns (4 per thread) and a strip of rows, keeps rows
+// r-1, r, r+1 of both iterates in registers, takes horizontal neighbours by
+// warp shuffles and the halos by lanes 0 and 31. The H terms of a row's four
+// sites are summed plainly and then added with Kahan compensation; the update
+// takes the prescaled fast cube root of the DOCH step kernels.
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+__device__ __forceinline__ float lat_byte(int v, int k) { return static_cast<float>((v << (24 - 8 * k)) >> 24); }
+
+// u = right x_r + left x_l + down x_d + up x_u (the order of the lattice step kernels)
+__device__ __forceinline__ float lat_sum(float wr, float xr, float wl, float xl, float wd, float xd, float wu,
+                                         float xu) {
+    return wr * xr + wl * xl + wd * xd + wu * xu;
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(kAThreads, 3)
+adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float *__restrict__ x2,
+              const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc, int tiles, int bpt,
+              float c, const float *__restrict__ alpha_tab, const float *__restrict__ zs_tab,
+              const float *__restrict__ xsc_tab, const int *__restrict__ dec, double *__restrict__ partials) {
+    const int tile = blockIdx.x % tiles;
+    const int part = blockIdx.x / tiles;
+    const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
+    const int r1 = static_cast<int>(static_cast<int64_t>(Lr) * (part + 1) / bpt);
+    const int ncol4 = Lc >> 2;
+    const int c4raw = tile * kAThreads + threadIdx.x;
+    const bool active = c4raw < ncol4;
+    const int c4 = c4raw % ncol4;
+    const int col = c4 * 4;
+    const int lane = threadIdx.x & 31;
+    const bool is_l = lane == 0, is_r = lane == 31;
+    const int hcol = is_l ? (col == 0 ? Lc - 1 : col - 1) : (col + 4 >= Lc ? 0 : col + 4);
+    const int64_t n = static_cast<int64_t>(Lr) * Lc;
+    auto ld4 = [&](const float *f, int64_t o) -> float4 { return __ldg(reinterpret_cast<const float4 *>(f + col + o)); };
+    auto ldh = [&](const float *f, int64_t o) -> float { return (is_l || is_r) ? __ldg(f + hcol + o) : 0.f; };
+    auto ldw = [&](const int8_t *p, int64_t o) -> int { return __ldg(reinterpret_cast<const int *>(p + col + o)); };
+    const bool use_y = UPDATE ? dec[0] != 0 : false;
+    const float alpha = UPDATE ? alpha_tab[0] : 0.f;
+    const float zs = UPDATE ? zs_tab[0] : 0.f, xsc = UPDATE ? xsc_tab[0] : 0.f;  // prescaled cube root
+    // FP32 sums with Kahan compensation: x^4, x^2, x u, y^4, y^2, y Jy
+    float acc[6], cmp[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = cmp[k] = 0.f;
+    auto add = [&](int k, float v) {
+        const float y = v - cmp[k];
+        const float t = acc[k] + y;
+        cmp[k] = (t - acc[k]) - y;
+        acc[k] = t;
+    };
+    if (r0 < r1) {
+        int64_t o = static_cast<int64_t>(r0) * Lc;
+        const int64_t ou = o == 0 ? n - Lc : o - Lc;
+        int64_t od = o + Lc == n ? 0 : o + Lc;
+        float4 au = ld4(x1, ou), am = ld4(x1, o), ad = ld4(x1, od);
+        float4 bu = ld4(x0, ou), bm = ld4(x0, o), bd = ld4(x0, od);
+        float ahm = ldh(x1, o), bhm = ldh(x0, o);
+        float du[4];
+        {
+            const int w = ldw(down, ou);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) du[q] = lat_byte(w, q);
+        }
+        int dm = ldw(down, o), rt = ldw(right, o);
+        float wl_h = is_l ? static_cast<float>(__ldg(right + hcol + o)) : 0.f;
+        float ahd = ldh(x1, od), bhd = ldh(x0, od);
+        for (int r = r0; r < r1; ++r) {
+            const int64_t onn = od + Lc == n ? 0 : od + Lc;
+            // loads of the next row, one row ahead
+            float4 an = ad, bn = bd;
+            int dn = dm, rn = rt;
+            float wn = wl_h, ahn = ahd, bhn = bhd;
+            if (r + 1 < r1) {
+                an = ld4(x1, onn);
+                bn = ld4(x0, onn);
+                dn = ldw(down, od);
+                rn = ldw(right, od);
+                wn = is_l ? static_cast<float>(__ldg(right + hcol + od)) : 0.f;
+                ahn = ldh(x1, onn);
+                bhn = ldh(x0, onn);
+            }
+            float axl = __shfl_up_sync(kFullMask, am.w, 1), axr = __shfl_down_sync(kFullMask, am.x, 1);
+            float bxl = __shfl_up_sync(kFullMask, bm.w, 1), bxr = __shfl_down_sync(kFullMask, bm.x, 1);
+            const int rtl = __shfl_up_sync(kFullMask, rt, 1);
+            float wleft = lat_byte(rtl, 3);
+            if (is_l) {
+                axl = ahm;
+                bxl = bhm;
+                wleft = wl_h;
+            }
+            if (is_r) {
+                axr = ahm;
+                bxr = bhm;
+            }
+            float wr[4], dd[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wr[q] = lat_byte(rt, q);
+                dd[q] = lat_byte(dm, q);
+            }
+            const float am_[4] = {am.x, am.y, am.z, am.w}, bm_[4] = {bm.x, bm.y, bm.z, bm.w};
+            const float au_[4] = {au.x, au.y, au.z, au.w}, bu_[4] = {bu.x, bu.y, bu.z, bu.w};
+            const float ad_[4] = {ad.x, ad.y, ad.z, ad.w}, bd_[4] = {bd.x, bd.y, bd.z, bd.w};
+            float out[4], rs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this row's four sites, then one compensated add
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float wlq = q == 0 ? wleft : wr[q - 1];
+                const float axr_q = q == 3 ? axr : am_[q + 1], axl_q = q == 0 ? axl : am_[q - 1];
+                const float bxr_q = q == 3 ? bxr : bm_[q + 1], bxl_q = q == 0 ? bxl : bm_[q - 1];
+                const float u1 = lat_sum(wr[q], axr_q, wlq, axl_q, dd[q], ad_[q], du[q], au_[q]);
+                const float u0 = lat_sum(wr[q], bxr_q, wlq, bxl_q, dd[q], bd_[q], du[q], bu_[q]);
+                const float xv = am_[q];
+                const float y = xv + c * (xv - bm_[q]);
+                const float jy = (1.f + c) * u1 - c * u0;
+                if (UPDATE) {
+                    const float v = use_y ? y : xv, jv = use_y ? jy : u1;
+                    out[q] = cbrt_pow2((jv + alpha * v) * zs) * xsc;
+                } else {
+                    const float x2v = xv * xv, y2 = y * y;
+                    rs[0] += x2v * x2v;
+                    rs[1] += x2v;
+                    rs[2] += xv * u1;
+                    rs[3] += y2 * y2;
+                    rs[4] += y2;
+                    rs[5] += y * jy;
+                }
+            }
+            if (!UPDATE) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) add(k, rs[k]);
+            }
+            if (UPDATE && active) __stcs(reinterpret_cast<float4 *>(x2 + col + o), make_float4(out[0], out[1], out[2], out[3]));
+            au = am;
+            am = ad;
+            ad = an;
+            bu = bm;
+            bm = bd;
+            bd = bn;
+            ahm = ahd;
+            bhm = bhd;
+            ahd = ahn;
+            bhd = bhn;
+            dm = dn;
+            rt = rn;
+            wl_h = wn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) du[q] = dd[q];
+            o = od;
+            od = onn;
+        }
+    }
+    if (UPDATE) return;
+    // block sums in FP64 in a fixed order; inactive lanes (wrapped columns) add nothing
+    __shared__ double red[kAThreads / 32][kTerms];
+    const int warp = threadIdx.x >> 5;
+    constexpr int kMap[6] = {0, 1, 2, 4, 5, 6};  // the terms of adoch_decide (no field on a lattice)
+#pragma unroll
+    for (int k = 0; k < kTerms; ++k) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (kMap[j] == k && active) v = static_cast<double>(acc[j]) - static_cast<double>(cmp[j]);
+        v = warp_sum(v);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kTerms) {
+        double t = 0.0;
+        for (int w = 0; w < kAThreads / 32; ++w) t += red[w][threadIdx.x];
+        partials[static_cast<int64_t>(blockIdx.x) * kTerms + threadIdx.x] = t;
+    }
+}
+
+struct LatticeShape {
+    int tiles = 0, bpt = 0, blocks = 0;
+};
+
+LatticeShape lattice_shape(const ising_context *c) {
+    static int occ = 0;
+    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adoch_lattice<true>, kAThreads, 0) !=
+                     cudaSuccess || occ < 1))
+        occ = 1;
+    LatticeShape s;
+    const int64_t ncol4 = c->l_cols / 4;
+    s.tiles = static_cast<int>((ncol4 + kAThreads - 1) / kAThreads);
+    int64_t bpt = static_cast<int64_t>(c->num_sms) * occ / s.tiles;
+    if (bpt < 1) bpt = 1;
+    if (bpt > c->l_rows) bpt = c->l_rows;
+    s.bpt = static_cast<int>(bpt);
+    s.blocks = static_cast<int>(bpt * s.tiles);
+    return s;
+}
+
+bool lattice_fast_ok(const ising_context *c, const void *x, int R) {
+    return c->format == ISING_FMT_TORUS2D && R == 1 && c->l_cols % 4 == 0 && c->l_rows >= 2 &&
+           c->l_rows < (1LL << 31) && c->l_cols < (1LL << 31) && reinterpret_cast<uintptr_t>(x) % 16 == 0;
+}
+
+ising_status_t adoch_lattice_run(ising_context *c, float *x, const ParamTabs &p, int iters, int q, int8_t *acc_dev,
+                                 double *H_dev, cudaStream_t st) {
+    const int64_t count = c->n;
+    const LatticeShape sh = lattice_shape(c);
+    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t xb = al(sizeof(float) * count);
+    const size_t pb = al(sizeof(double) * static_cast<size_t>(sh.blocks) * kTerms);
+    const size_t hb = al(sizeof(double) * static_cast<size_t>(q + 1));
+    const size_t db = al(sizeof(int));
+    DOCH_CHECK(c->ckpt.ensure(2 * xb + pb + hb + db));
+    unsigned char *base = c->ckpt.as<unsigned char>();
+    float *x1 = x, *x0 = reinterpret_cast<float *>(base), *x2 = reinterpret_cast<float *>(base + xb);
+    double *part = reinterpret_cast<double *>(base + 2 * xb);
+    double *hist = reinterpret_cast<double *>(base + 2 * xb + pb);
+    int *dec = reinterpret_cast<int *>(base + 2 * xb + pb + hb);
+    DOCH_CUDA(cudaMemcpyAsync(x0, x1, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));  // x^{-1} := x^0
+    const int Lr = static_cast<int>(c->l_rows), Lc = static_cast<int>(c->l_cols);
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+        const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+        const float ck = static_cast<float>(k >= 1 ? (t - 1.0) / t_next : 0.0);
+        adoch_lattice<false><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, nullptr, c->right, c->down, Lr, Lc, sh.tiles,
+                                                            sh.bpt, ck, nullptr, nullptr, nullptr, nullptr, part);
+        DOCH_CUDA(cudaGetLastError());
+        adoch_decide<<<1, kDThreads, 0, st>>>(part, 1, 1, sh.blocks, p.alpha_d, p.beta_d, k, q, hist, dec, acc_dev,
+                                              H_dev);
+        DOCH_CUDA(cudaGetLastError());
+        adoch_lattice<true><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, x2, c->right, c->down, Lr, Lc, sh.tiles,
+                                                           sh.bpt, ck, p.alpha_f, p.zscale_f, p.xscale_f, dec,
+                                                           nullptr);
+        DOCH_CUDA(cudaGetLastError());
+        float *tx = x0;  // x^{k-1} <- x^k <- x^{k+1}
+        x0 = x1;
+        x1 = x2;
+        x2 = tx;
+        t = t_next;
+    }
+    if (x1 != x) DOCH_CUDA(cudaMemcpyAsync(x, x1, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));
+    return ISING_OK;
+}
+
 template <typename XT, typename Fn>
 ising_status_t adoch_run(ising_context *c, const Fn &fn, XT *x, int R, const ParamTabs &p, const XT *h_x,
                          int iters, int q, int8_t *acc_dev, double *H_dev, cudaStream_t st) {
@@ -314,6 +561,8 @@ ising_status_t adoch_dispatch(ising_context *c, XT *x, int R, const ParamTabs &p
 
 ising_status_t adoch_iterate(ising_context *c, void *x, int xtype, int R, const ParamTabs &p, int iters, int q,
                              int8_t *acc_dev, double *H_dev, cudaStream_t st) {
+    if (xtype == ISING_F32 && lattice_fast_ok(c, x, R))
+        return adoch_lattice_run(c, static_cast<float *>(x), p, iters, q, acc_dev, H_dev, st);
     if (xtype == ISING_F32)
         return adoch_dispatch<float>(c, static_cast<float *>(x), R, p, c->has_h ? c->h_f32 : nullptr, iters, q,
                                      acc_dev, H_dev, st);

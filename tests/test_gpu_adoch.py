@@ -108,6 +108,33 @@ def test_adoch_fp32_matches_oracle():
     _check(P, x0.astype(np.float64), alpha, beta, iters, q, x, acc, None, 1e-5, 1e-4)
 
 
+@pytest.mark.parametrize("shape,q", [((64, 128), 1), ((37, 200), 5), ((16, 1024), 3), ((30, 42), 2)])
+def test_adoch_lattice_fp32(shape, q):
+    """FP32 lattice: l_cols % 4 == 0 with a 16-byte aligned iterate takes the fast path (both coupling
+    products recomputed in each pass, nothing stored); (30, 42) and an iterate shifted by one float
+    take the general kernels."""
+    J = I.torus_pm1(*shape, seed=251)
+    R, iters = 1, 40
+    x0 = I.x0_uniform(J.n, R, seed=252)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    P = O.Problem(J)
+    x, acc, H = _run(J, x0, [alpha], [beta], iters, q)
+    clear = _check(P, x0.astype(np.float64), alpha, beta, iters, q, x, acc, None, 1e-5, 1e-4)
+    assert clear[:10].all()
+    # the same run from a misaligned iterate (general kernels)
+    hd = N.ising_create(N.Problem(J))
+    try:
+        buf = torch.zeros(J.n + 1, dtype=torch.float32, device="cuda")
+        xs = buf[1:].view(J.n, 1)
+        xs.copy_(torch.from_numpy(x0))
+        acc2 = torch.zeros((iters, 1), dtype=torch.int8, device="cuda")
+        N.ising_iterate_adoch(hd, xs, [alpha], [beta], iters, q, accepted=acc2)
+        x2, a2 = xs.cpu().numpy(), acc2.cpu().numpy()
+    finally:
+        N.ising_destroy(hd)
+    _check(P, x0.astype(np.float64), alpha, beta, iters, q, x2, a2, None, 1e-5, 1e-4)
+
+
 def test_adoch_q0_never_rises():
     J = I.erdos_renyi_pm1(400, 0.04, seed=221)
     R, iters = 6, 60
