@@ -455,8 +455,21 @@ class Backward:
             ev_b.record(stream)
 
     def roofline(self, per_launch_s):
-        # whole call / 3 x iters launches: average launch of the forward, recompute and adjoint steps
-        return None
+        # per step index k the call runs a forward step, a recompute step and an adjoint step; unique
+        # bytes: forward and recompute read and write x (2 n R 4 B each) and read the CSR arrays; the
+        # adjoint reads g^(k+1), x^(k+1), x^k and writes g^k (4 n R 4 B) and reads the CSR arrays.
+        # The 25.6 MB iterates stay in L2, so this is the HBM-equivalent rate of the whole step triple.
+        peak, kind = measured_peaks()
+        nnz = 3 * self.n
+        csr = nnz * (4 + 1) + (self.n + 1) * 8
+        xb = self.n * self.R * 4
+        alg = 2 * (2 * xb + csr) + (4 * xb + csr)
+        ach = alg / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "csr_step_kernel (forward, recompute) + adjoint_step_kernel",
+                "peak_kind": kind, "algorithmic_bytes_per_launch": alg,
+                "launch": "one step index: forward step + recompute step + adjoint step",
+                "note": "iterates L2-resident: an HBM-equivalent rate of unique bytes"}
 
     def e2e(self, n_steps, sid):
         N = self.N
@@ -497,6 +510,7 @@ class Er800:
     def __init__(self, args, rank, N, I, torch):
         g = I.erdos_renyi_pm1(800, 0.06, seed=1 + 1000 * rank)
         self.n, self.R, self.iters = g.n, 8, 1000
+        self.nnz = int(g.row_ptr[-1])
         prob = N.Problem(g)
         self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=1)
         self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
@@ -525,7 +539,18 @@ class Er800:
         N.ising_energy(self.h, self.x, E_int=self.E, cut_int=self.cut, best=self.best, stream=sid)
 
     def roofline(self, per_launch_s):
-        return None
+        # FP64 arithmetic of the 1000 steps in the one launch: a multiply-add per stored coupling and
+        # replica, and alpha x, the scale and the cube root's argument per spin and replica (cube root
+        # not counted); against the nominal dense FP64 rate of the part (1.25 TFLOP/s). One CTA per
+        # replica (8 of 152 SMs) holds the iterate in shared memory: the launch is latency-bound.
+        nnz = self.nnz
+        flops = self.iters * self.R * (2.0 * nnz + 3.0 * self.n)
+        ach = flops / per_launch_s / 1e9
+        peak = 1250.0
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": "nominal FP64 (1.25 TFLOP/s)",
+                "algorithmic_flops_per_launch": flops,
+                "note": "one CTA per replica on 8 of 152 SMs; latency-bound"}
 
     def e2e(self, n_steps, sid):
         N = self.N
