@@ -68,8 +68,9 @@ typedef enum {
     ISING_FMT_CSR = 0,     /* compressed sparse rows (Supplementary Note 9)            */
     ISING_FMT_TORUS2D = 1, /* periodic 2-D lattice, one coupling per lattice edge      */
     ISING_FMT_DENSE = 2,   /* full n x n row-major matrix                               */
-    ISING_FMT_PROCEDURAL = 3 /* J_ij = sin(i j + c), generated on the fly (handles from
+    ISING_FMT_PROCEDURAL = 3,/* J_ij = sin(i j + c), generated on the fly (handles from
                                 ising_create_procedural only)                           */
+    ISING_FMT_ELL = 4        /* fixed-width rows (converted to CSR by ising_create)      */
 } ising_format_t;
 
 /* Element types. */
@@ -105,10 +106,16 @@ enum {
  *   right[r][c] couples (r, c) with (r, (c+1) mod l_cols) and down[r][c]
  *   couples (r, c) with ((r+1) mod l_rows, c); jtype I8. l_rows, l_cols >= 2
  *   (on a 2-wide side both edges of a pair add up to one J_ij).
- * DENSE: dense[i * n + j] = J_ij, jtype I8, F32 or F64.
+ * ELL: row i holds the ell_width slots col[i * ell_width + k] (int32; -1
+ *   marks an empty slot) with values val[i * ell_width + k] of jtype (I8, I16,
+ *   I32, F32 or F64); converted to CSR on create, so everything CSR accepts
+ *   (batches included) applies.
+ * DENSE: dense[i * n + j] = J_ij, jtype I8, I16, I32, FP8E4M3, BF16, F32 or
+ *   F64; every value must be an integer with |J_ij| <= 256 (held exactly in
+ *   BF16, or as 2-bit codes when all are -1, 0 or +1).
  * Field: h[n] of type htype (I8, I16, I32, F32, F64), or NULL for h = 0
  *   (CSR and DENSE; a TORUS2D lattice takes no field).
- * Batches: n_instances > 1 (CSR only) concatenates independent problems;
+ * Batches: n_instances > 1 (CSR or ELL) concatenates independent problems;
  *   instance b owns spins [inst_offset[b], inst_offset[b+1]) and its rows may
  *   only reference columns of that range. n_instances = 0 or 1 means one
  *   instance and inst_offset may be NULL.
@@ -128,6 +135,7 @@ typedef struct {
     int32_t htype;           /* ising_dtype_t of h */
     int32_t n_instances;     /* 0 or 1: single instance */
     const int64_t *inst_offset; /* [n_instances + 1] or NULL */
+    int64_t ell_width;       /* ELL: slots per row */
 } ising_problem_t;
 
 typedef struct ising_context *ising_handle_t;
@@ -150,7 +158,7 @@ ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double e
  * Validate J and h (symmetry, zero diagonal, index ranges, finite values;
  * skipped with ISING_FLAG_SKIP_VALIDATION) and copy them to device memory
  * owned by a new handle. Dense couplings must be integers with |J| <= 256
- * (ISING_ERR_UNSUPPORTED otherwise); they are held in the tensor-core tile
+ * (ISING_ERR_UNSUPPORTED otherwise, whatever their storage type); they are held in the tensor-core tile
  * order, as packed 2-bit codes when every entry is -1, 0 or +1 and as BF16
  * otherwise (both exact). On failure *out is NULL.
  */
@@ -178,8 +186,8 @@ ISING_API ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int
  * product for one replica (each serves J_ij x_j and J_ji x_i; order-independent
  * int64 fixed-point sums), n^2 for more.
  *   n       2 .. 2^30 spins;  c  0 .. 2^40 (the paper uses 100).
- * The handle supports ising_iterate (F32 iterates, no H_trace),
- * ising_iterate_until (F32), ising_energy (E_f64, cut_f64, best, spins; the
+ * The handle supports ising_iterate (F32 iterates),
+ * ising_iterate_adoch (F32), ising_iterate_until (F32), ising_energy (E_f64, cut_f64, best, spins; the
  * sum of J in the cut is evaluated in closed form in FP64) and
  * ising_params_device (Wigner estimate; method 1 is ISING_ERR_UNSUPPORTED).
  * Creation costs O(n) host work (closed-form sums of J and J^2).
@@ -224,7 +232,8 @@ ISING_API void ising_destroy(ising_handle_t h);
  *          on the device, fused into the iteration kernel.
  * For DENSE the iterate is BF16 and the coupling product runs on the
  * tcgen05 tensor cores with FP32 accumulation. For PROCEDURAL the iterate is
- * F32, H_trace must be NULL, and each step generates all n^2 couplings.
+ * F32 and each step generates the couplings; an H_trace costs one more
+ * coupling product per step.
  */
 ISING_API ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                              const double *alpha, int32_t alpha_len, const double *beta,
@@ -248,9 +257,10 @@ ISING_API ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype,
  *          1 where v^k = y^k.
  *   H_trace   NULL, or [iters + 1][max(1,n_instances)][R] FP64 (host or
  *          device): H(x^(k)) for k = 0 .. iters.
- * CSR and TORUS2D couplings; ISING_ERR_UNSUPPORTED for DENSE. Device
- * scratch: four iterate-sized buffers plus O(R) reduction space, owned by
- * the handle.
+ * CSR, TORUS2D and PROCEDURAL (F32) couplings; ISING_ERR_UNSUPPORTED for
+ * DENSE. Device scratch: four iterate-sized buffers plus O(R) reduction
+ * space, owned by the handle (two for an FP32 lattice with R = 1, whose
+ * passes recompute both coupling products instead of storing them).
  */
 ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int32_t R,
                                    const double *alpha, const double *beta, int32_t iters, int32_t q,

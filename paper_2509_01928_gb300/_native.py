@@ -24,7 +24,7 @@ STATUS_NAMES = {
     6: "ISING_ERR_OOM", 7: "ISING_ERR_CUDA", 8: "ISING_ERR_TIMEOUT", 9: "ISING_ERR_NOT_MONOTONE",
     10: "ISING_ERR_UNSUPPORTED",
 }
-FMT_CSR, FMT_TORUS2D, FMT_DENSE, FMT_PROCEDURAL = 0, 1, 2, 3
+FMT_CSR, FMT_TORUS2D, FMT_DENSE, FMT_PROCEDURAL, FMT_ELL = 0, 1, 2, 3, 4
 I8, I16, I32, FP8E4M3, BF16, F32, F64 = range(7)
 FLAG_ASYNC, FLAG_SKIP_VALIDATION, FLAG_STRICT_MONOTONE, FLAG_SINGLE_STEP = 1, 2, 4, 8
 
@@ -37,7 +37,7 @@ class IsingProblem(ctypes.Structure):
         ("row_ptr", _vp), ("col", _vp), ("val", _vp),
         ("l_rows", ctypes.c_int64), ("l_cols", ctypes.c_int64), ("right", _vp), ("down", _vp),
         ("dense", _vp), ("h", _vp), ("htype", ctypes.c_int32), ("n_instances", ctypes.c_int32),
-        ("inst_offset", _vp),
+        ("inst_offset", _vp), ("ell_width", ctypes.c_int64),
     ]
 
 
@@ -122,6 +122,8 @@ def _dtype_code(a) -> int:
         import torch
         table = {torch.int8: I8, torch.int16: I16, torch.int32: I32, torch.bfloat16: BF16,
                  torch.float32: F32, torch.float64: F64}
+        if hasattr(torch, "float8_e4m3fn"):
+            table[torch.float8_e4m3fn] = FP8E4M3
         return table[a.dtype]
     table = {np.dtype(np.int8): I8, np.dtype(np.int16): I16, np.dtype(np.int32): I32,
              np.dtype(np.float32): F32, np.dtype(np.float64): F64}
@@ -163,14 +165,19 @@ def _f64(a, count=None):
 class Problem:
     """Marshals a coupling matrix into an ising_problem_t (keeps the arrays alive).
 
-    J: an object with row_ptr/col/val (CSR), one with right/down (2-D torus),
-    or a square array (dense). instances: optional spin offsets [B + 1] for a
-    batch of CSR instances concatenated along n.
+    J: an object with row_ptr/col/val (CSR), one with ell_col/ell_val ([n][w]
+    ELL rows, column -1 for an empty slot), one with right/down (2-D torus), or
+    a square array (dense). instances: optional spin offsets [B + 1] for a
+    batch of CSR/ELL instances concatenated along n. jtype overrides the type
+    code of J's values (e.g. FP8E4M3 for raw E4M3 bytes held in a uint8 array).
     """
 
-    def __init__(self, J, h=None, instances=None):
+    def __init__(self, J, h=None, instances=None, jtype=None):
         s = IsingProblem()
         keep = []
+
+        def code(a):
+            return _dtype_code(a) if jtype is None else int(jtype)
 
         def arr(a, dtype=None):
             if _is_torch(a):
@@ -185,19 +192,25 @@ class Problem:
             col = arr(J.col, np.int32)
             val = arr(J.val)
             s.n = int(rp.shape[0]) - 1
-            s.format, s.jtype = FMT_CSR, _dtype_code(val)
+            s.format, s.jtype = FMT_CSR, code(val)
             s.row_ptr, s.col, s.val = _ptr(rp), _ptr(col), _ptr(val)
+        elif hasattr(J, "ell_col"):
+            col = arr(J.ell_col, np.int32)
+            val = arr(J.ell_val)
+            s.n, s.ell_width = int(col.shape[0]), int(col.shape[1])
+            s.format, s.jtype = FMT_ELL, code(val)
+            s.col, s.val = _ptr(col), _ptr(val)
         elif hasattr(J, "right"):
             r = arr(J.right)
             d = arr(J.down)
             lr, lc = r.shape
             s.n, s.l_rows, s.l_cols = lr * lc, lr, lc
-            s.format, s.jtype = FMT_TORUS2D, _dtype_code(r)
+            s.format, s.jtype = FMT_TORUS2D, code(r)
             s.right, s.down = _ptr(r), _ptr(d)
         else:
             D = arr(J)
             s.n = int(D.shape[0])
-            s.format, s.jtype = FMT_DENSE, _dtype_code(D)
+            s.format, s.jtype = FMT_DENSE, code(D)
             s.dense = _ptr(D)
         if h is not None:
             hh = arr(h)

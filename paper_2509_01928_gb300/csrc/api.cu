@@ -88,6 +88,16 @@ ising_status_t to_host(const void *src, size_t bytes, std::vector<unsigned char>
     return ISING_OK;
 }
 
+// FP8 E4M3 (OCP "fn" variant: bias 7, no infinities, S.1111.111 is NaN)
+double fp8e4m3_value(uint8_t b) {
+    const int e = (b >> 3) & 15, m = b & 7;
+    double v;
+    if (e == 15 && m == 7) v = NAN;
+    else if (e == 0) v = std::ldexp(static_cast<double>(m), -9);
+    else v = std::ldexp(1.0 + m / 8.0, e - 7);
+    return (b & 0x80) ? -v : v;
+}
+
 double value_at(const unsigned char *base, int t, int64_t i) {
     switch (t) {
         case ISING_I8: return reinterpret_cast<const int8_t *>(base)[i];
@@ -95,6 +105,13 @@ double value_at(const unsigned char *base, int t, int64_t i) {
         case ISING_I32: return reinterpret_cast<const int32_t *>(base)[i];
         case ISING_F32: return reinterpret_cast<const float *>(base)[i];
         case ISING_F64: return reinterpret_cast<const double *>(base)[i];
+        case ISING_FP8E4M3: return fp8e4m3_value(base[i]);
+        case ISING_BF16: {
+            const uint32_t u = static_cast<uint32_t>(reinterpret_cast<const uint16_t *>(base)[i]) << 16;
+            float f;
+            std::memcpy(&f, &u, 4);
+            return f;
+        }
         default: return NAN;
     }
 }
@@ -127,9 +144,46 @@ struct HostProblem {
     int64_t l_rows = 0, l_cols = 0;
 };
 
+ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem &hp);
+
+// ELL rows -> CSR on the host (empty slots, col = -1, dropped), then the CSR path
+ising_status_t load_ell(const ising_problem_t *p, bool validate, HostProblem &hp) {
+    const int64_t n = p->n, w = p->ell_width;
+    if (w < 0 || (w > 0 && (!p->col || !p->val))) return fail(ISING_ERR_INVALID_ARG, "ELL arrays are NULL");
+    if (p->jtype == ISING_FP8E4M3 || p->jtype == ISING_BF16)
+        return fail(ISING_ERR_UNSUPPORTED, "ELL values must be I8/I16/I32/F32/F64");
+    const size_t jsz = dtype_size(p->jtype);
+    std::vector<unsigned char> col_raw, val_raw;
+    DOCH_CHECK(to_host(p->col, sizeof(int32_t) * n * w, col_raw));
+    DOCH_CHECK(to_host(p->val, jsz * n * w, val_raw));
+    const int32_t *cl = reinterpret_cast<const int32_t *>(col_raw.data());
+    std::vector<int64_t> rp(n + 1, 0);
+    std::vector<int32_t> col;
+    std::vector<unsigned char> val;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < w; ++k) {
+            const int32_t j = cl[i * w + k];
+            if (j == -1) continue;
+            if (j < 0 || j >= n) return fail(ISING_ERR_INDEX_RANGE, "ELL column out of range in row " + std::to_string(i));
+            col.push_back(j);
+            val.insert(val.end(), &val_raw[(i * w + k) * jsz], &val_raw[(i * w + k) * jsz] + jsz);
+        }
+        rp[i + 1] = static_cast<int64_t>(col.size());
+    }
+    ising_problem_t q = *p;
+    q.format = ISING_FMT_CSR;
+    q.row_ptr = rp.data();
+    q.col = col.data();
+    q.val = val.data();
+    q.ell_width = 0;
+    DOCH_CHECK(load_problem(&q, validate, hp));
+    return ISING_OK;
+}
+
 ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem &hp) {
     if (!p) return fail(ISING_ERR_INVALID_ARG, "problem is NULL");
     if (p->n < 1) return fail(ISING_ERR_INVALID_ARG, "n must be >= 1");
+    if (p->format == ISING_FMT_ELL) return load_ell(p, validate, hp);
     hp.n = p->n;
     hp.format = p->format;
     hp.jtype = p->jtype;
@@ -223,10 +277,15 @@ ising_status_t load_problem(const ising_problem_t *p, bool validate, HostProblem
         DOCH_CHECK(to_host(p->down, n, hp.down));
     } else if (p->format == ISING_FMT_DENSE) {
         if (!p->dense) return fail(ISING_ERR_INVALID_ARG, "dense array is NULL");
-        if (p->jtype != ISING_I8 && p->jtype != ISING_I16 && p->jtype != ISING_I32)
-            return fail(ISING_ERR_UNSUPPORTED,
-                        "DENSE couplings must be integers (held exactly as BF16 for the tensor cores)");
         DOCH_CHECK(to_host(p->dense, jsz * n * n, hp.dense));
+        // the storage (2-bit codes or BF16) is exact only for integers of magnitude <= 256: checked
+        // for every type, with or without validation
+        for (int64_t e = 0; e < n * n; ++e) {
+            const double v = value_at(hp.dense.data(), p->jtype, e);
+            if (!(std::fabs(v) <= 256.0) || v != std::floor(v))
+                return fail(ISING_ERR_UNSUPPORTED,
+                            "DENSE couplings must be integers with |J_ij| <= 256 (held exactly in BF16)");
+        }
         if (validate) {
             for (int64_t i = 0; i < n; ++i) {
                 if (value_at(hp.dense.data(), p->jtype, i * n + i) != 0.0)
@@ -401,6 +460,7 @@ void destroy_ctx(ising_context *c) {
     c->batch_items.release();
     c->proc_units.release();
     c->proc_acc.release();
+    c->proc_u.release();
     delete c;
 }
 
@@ -416,7 +476,8 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
     c->max_inst_n = 0;
     for (int b = 0; b < hp.n_inst; ++b) c->max_inst_n = std::max(c->max_inst_n, hp.off[b + 1] - hp.off[b]);
     c->has_h = !hp.h.empty();
-    c->integer = dtype_integer(hp.jtype) && (!c->has_h || dtype_integer(hp.htype));
+    // DENSE values are integers whatever their storage type (checked on load)
+    c->integer = (dtype_integer(hp.jtype) || hp.format == ISING_FMT_DENSE) && (!c->has_h || dtype_integer(hp.htype));
     DOCH_CHECK(upload(&c->inst_off, hp.off.data(), sizeof(int64_t) * hp.off.size()));
     if (hp.format == ISING_FMT_CSR && hp.n_inst > 1) {
         // longest-first queue order for the persistent batched kernel
@@ -937,7 +998,6 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
         if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
     } else if (h->format == ISING_FMT_PROCEDURAL) {
         if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
-        if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for PROCEDURAL couplings");
     } else if (xtype != ISING_F32 && xtype != ISING_F64) {
         return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
     }
@@ -1041,8 +1101,10 @@ ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int
         return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, iters >= 0 and q >= 0");
     if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
     ising_context *c = h;
-    if (c->format != ISING_FMT_CSR && c->format != ISING_FMT_TORUS2D)
-        return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR or TORUS2D couplings");
+    if (c->format != ISING_FMT_CSR && c->format != ISING_FMT_TORUS2D && c->format != ISING_FMT_PROCEDURAL)
+        return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR, TORUS2D or PROCEDURAL couplings");
+    if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
+        return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t count = c->n * R;
     const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);

@@ -100,6 +100,7 @@ struct ising_context {
     doch::DevBuf proc_units;
     int proc_units_count = 0;
     doch::DevBuf proc_acc;
+    doch::DevBuf proc_u;  // J x for the H monitor
     // field (both precisions; integer copy when integral)
     float *h_f32 = nullptr;
     double *h_f64 = nullptr;
@@ -253,7 +254,11 @@ ising_status_t proc_step(ising_context *c, const float *x_in, float *x_out, int 
                          cudaStream_t st);
 ising_status_t proc_energy(ising_context *c, const void *x, int xtype, int R, double *E_d, double *cut_d,
                            cudaStream_t st);
-ising_status_t proc_params(const ising_context *c, double eta, double *alpha, double *beta);
+ising_status_t proc_params(ising_context *c, double eta, double *alpha, double *beta);
+// u = J x (FP32, [n][R], device), the coupling product alone (ADOCH passes)
+ising_status_t proc_product(ising_context *c, const float *x, float *u, int R, cudaStream_t st);
+ising_status_t proc_hamiltonian(ising_context *c, const float *x, int R, const ParamTabs &p, int k, double *H_out,
+                                cudaStream_t st);
 void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2);
 
 // Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64

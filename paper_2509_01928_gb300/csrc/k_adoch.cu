@@ -50,6 +50,7 @@ struct CsrProduct {
     const int32_t *col;
     const VT *val;
     static constexpr bool kGrid = false;
+    static constexpr bool kStored = false;
     __device__ XT operator()(const XT *x, int64_t i, int64_t, int64_t, int r, int R) const {
         XT acc = XT(0);
         const int64_t e1 = row_ptr[i + 1];
@@ -64,6 +65,7 @@ struct TorusProduct {
     const int8_t *right, *down;
     int64_t Lr, Lc;
     static constexpr bool kGrid = true;  // wants the (row, column) of site i
+    static constexpr bool kStored = false;
     __device__ XT operator()(const XT *x, int64_t i, int64_t rr, int64_t cc, int r, int R) const {
         const int64_t s_l = rr * Lc + (cc == 0 ? Lc - 1 : cc - 1);
         const int64_t s_r = rr * Lc + (cc + 1 == Lc ? 0 : cc + 1);
@@ -72,6 +74,14 @@ struct TorusProduct {
         return static_cast<XT>(right[i]) * x[s_r * R + r] + static_cast<XT>(right[s_l]) * x[s_l * R + r] +
                static_cast<XT>(down[i]) * x[s_d * R + r] + static_cast<XT>(down[s_u]) * x[s_u * R + r];
     }
+};
+
+// procedural couplings: u^k = J x^k is formed by the procedural product before the pass
+// (the pass reads it from u1 instead of computing it)
+struct ProcProduct {
+    static constexpr bool kGrid = false;
+    static constexpr bool kStored = true;
+    __device__ float operator()(const float *, int64_t, int64_t, int64_t, int, int) const { return 0.f; }
 };
 
 template <typename Acc>
@@ -116,8 +126,13 @@ adoch_pass(Fn fn, const XT *__restrict__ x1, const XT *__restrict__ x0, const XT
     }
     for (int64_t i = s0 + threadIdx.x; i < s1; i += kAThreads) {
         const int64_t at = i * R + r;
-        const XT u = fn(x1, i, rr, cc, r, R);
-        u1[at] = u;
+        XT u;
+        if constexpr (Fn::kStored) {
+            u = u1[at];
+        } else {
+            u = fn(x1, i, rr, cc, r, R);
+            u1[at] = u;
+        }
         const XT xv = x1[at];
         const XT y = xv + c * (xv - x0[at]);
         const XT jy = (XT(1) + c) * u - c * u0[at];
@@ -513,6 +528,9 @@ ising_status_t adoch_run(ising_context *c, const Fn &fn, XT *x, int R, const Par
     for (int k = 0; k < iters; ++k) {
         const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
         const XT ck = static_cast<XT>(k >= 1 ? (t - 1.0) / t_next : 0.0);
+        if constexpr (Fn::kStored) {
+            if constexpr (sizeof(XT) == 4) DOCH_CHECK(proc_product(c, x1, u1, R, st));
+        }
         adoch_pass<XT, Fn><<<grid, kAThreads, 0, st>>>(fn, x1, x0, u0, u1, h_d, off, c->n, R, chunks, ck, part);
         DOCH_CUDA(cudaGetLastError());
         adoch_decide<<<pairs, kDThreads, 0, st>>>(part, c->n_inst, R, chunks, p.alpha_d, p.beta_d, k, q, hist,
@@ -539,7 +557,14 @@ ising_status_t adoch_dispatch(ising_context *c, XT *x, int R, const ParamTabs &p
     if (c->format == ISING_FMT_TORUS2D)
         return adoch_run<XT>(c, TorusProduct<XT>{c->right, c->down, c->l_rows, c->l_cols}, x, R, p, h_x, iters,
                              q, acc_dev, H_dev, st);
-    if (c->format != ISING_FMT_CSR) return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR or TORUS2D couplings");
+    if (c->format == ISING_FMT_PROCEDURAL) {
+        if constexpr (sizeof(XT) == 4)
+            return adoch_run<XT>(c, ProcProduct{}, x, R, p, h_x, iters, q, acc_dev, H_dev, st);
+        else
+            return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+    }
+    if (c->format != ISING_FMT_CSR)
+        return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR, TORUS2D or PROCEDURAL couplings");
     switch (c->jtype) {
         case ISING_I8:
             return adoch_run<XT>(c, CsrProduct<XT, int8_t>{c->row_ptr, c->col, static_cast<const int8_t *>(c->val)},

@@ -26,7 +26,7 @@
 // order, so results do not depend on the schedule.
 // The sums of J and of J^2 over i != j (for the cut and the Wigner estimate)
 // come in closed form from geometric series of the sines, in FP64 on the host;
-// the rows' sums of |J_ij| (Eq. alphabeta) from a device pass.
+// the rows' sums of |J_ij| (Eq. alphabeta) from the symmetric product with |J|.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -231,36 +231,6 @@ proc_finish_quad(const float *__restrict__ part, int S, const int8_t *__restrict
     if (threadIdx.x == 0) qpart[static_cast<int64_t>(r) * gridDim.x + blockIdx.x] = red[0];
 }
 
-// per block: max over its rows of sum_{j != i} |J_ij| (per-tile FP32 sums, FP64 across tiles)
-__global__ void __launch_bounds__(kPT)
-proc_rowabs(int64_t n, int64_t offset, int n_tiles, double *__restrict__ bmax) {
-    const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kPT;
-    const int64_t i = row0 + threadIdx.x;
-    const uint64_t i1 = static_cast<uint64_t>(i) + 1;
-    const uint64_t D = phase64(i1);
-    uint64_t P = phase64(i1 + static_cast<uint64_t>(offset));
-    double a = 0.0;
-    for (int t = 0; t < n_tiles; ++t) {
-        const int64_t j0 = static_cast<int64_t>(t) * kPN;
-        const int cols = n - j0 < kPN ? static_cast<int>(n - j0) : kPN;
-        float ta = 0.f;
-        for (int jj = 0; jj < cols; ++jj) {
-            const float w = fabsf(coupling(static_cast<uint32_t>(P >> 32)));
-            P += D;
-            ta += (j0 + jj == i) ? 0.f : w;
-        }
-        a += ta;
-    }
-    __shared__ double red[kPT];
-    red[threadIdx.x] = i < n ? a : 0.0;
-    __syncthreads();
-    for (int w = kPT / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) bmax[blockIdx.x] = red[0];
-}
-
 // the couplings of rows row0.. and columns col0.. as the product kernels generate
 // them (64-bit phase at every 32nd column, 32-bit chain in between)
 __global__ void proc_couplings(int64_t row0, int rows, int64_t col0, int cols, int64_t offset,
@@ -279,6 +249,36 @@ __global__ void proc_couplings(int64_t row0, int rows, int64_t col0, int cols, i
         }
         out[static_cast<int64_t>(r) * cols + j] = row0 + r == col0 + j ? 0.f : coupling(t);
         t += d;
+    }
+}
+
+// H(x) of Eq. Hamilton per replica (no field), one block per replica, FP64 in a fixed order:
+// beta/4 sum x^4 - alpha/2 sum x^2 - 1/2 sum x u with u = J x
+__global__ void __launch_bounds__(kQT)
+proc_ham(const float *__restrict__ x, const float *__restrict__ u, int64_t n, int R, const double *__restrict__ alpha_d,
+         int alpha_len, int k, const double *__restrict__ beta_d, double *__restrict__ H_out) {
+    const int r = blockIdx.x;
+    double s4 = 0.0, s2 = 0.0, su = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kQT) {
+        const double xv = x[i * R + r];
+        const double x2 = xv * xv;
+        s4 += x2 * x2;
+        s2 += x2;
+        su += xv * static_cast<double>(u[i * R + r]);
+    }
+    __shared__ double red[3][kQT];
+    red[0][threadIdx.x] = s4;
+    red[1][threadIdx.x] = s2;
+    red[2][threadIdx.x] = su;
+    __syncthreads();
+    for (int w = kQT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int t = 0; t < 3; ++t) red[t][threadIdx.x] += red[t][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double a = alpha_d[k < alpha_len ? k : alpha_len - 1], b = beta_d[0];
+        H_out[r] = b / 4.0 * red[0][0] - a / 2.0 * red[1][0] - 0.5 * red[2][0];
     }
 }
 
@@ -379,7 +379,8 @@ __global__ void proc_maxabs(const float *__restrict__ x, int64_t n, unsigned *__
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as integers
 }
 
-template <typename XT, bool DIAG>
+// ABS: row and column sums of |J_ij| (x taken as all ones, not read)
+template <typename XT, bool DIAG, bool ABS>
 __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long long *__restrict__ acc, float scale,
                                          int4 un, int64_t n, int64_t offset) {
     __shared__ __align__(16) float xs[kSTC];
@@ -395,7 +396,7 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
 #pragma unroll
     for (int k = 0; k < kSR; ++k) {
         const int64_t i = r0 + threadIdx.x + kPT * k;
-        xr[k] = i < n ? static_cast<float>(x[i]) : 0.f;
+        xr[k] = i < n ? (ABS ? 1.f : static_cast<float>(x[i])) : 0.f;
         const uint64_t i1 = static_cast<uint64_t>(i) + 1;
         const uint64_t D = phase64(i1);
         D32[k] = 32 * D;
@@ -406,7 +407,7 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
     for (int tile = 0; tile < ntile; ++tile) {
         const int64_t c0 = c_begin + static_cast<int64_t>(tile) * kSTC;
         __syncthreads();
-        xs[threadIdx.x] = c0 + threadIdx.x < n ? static_cast<float>(x[c0 + threadIdx.x]) : 0.f;
+        xs[threadIdx.x] = c0 + threadIdx.x < n ? (ABS ? 1.f : static_cast<float>(x[c0 + threadIdx.x])) : 0.f;
         __syncthreads();
         float trs[kSR];
 #pragma unroll
@@ -430,6 +431,7 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
 #pragma unroll
                     for (int k = 0; k < kSR; ++k) {
                         float w = coupling(tk[k]);
+                        if (ABS) w = fabsf(w);
                         tk[k] += d[k];
                         if (DIAG && c0 + chunk * 32 + b == r0 + threadIdx.x + kPT * k) w = 0.f;
                         crs[k] = fmaf(w, xv[bb], crs[k]);
@@ -460,14 +462,54 @@ __device__ __forceinline__ void sym_unit(const XT *__restrict__ x, unsigned long
 }
 
 // unit: (row tile, first column tile, column tiles, 1 = diagonal block); m > 0: fixed max |x|
-template <typename XT>
+template <typename XT, bool ABS = false>
 __global__ void __launch_bounds__(kPT, 2)
 proc_sym(const XT *__restrict__ x, unsigned long long *__restrict__ acc, const unsigned *__restrict__ maxbits,
          float m, const int4 *__restrict__ units, int64_t n, int64_t offset) {
     const int4 un = units[blockIdx.x];
     const float scale = ldexpf(1.f, fixed_exp(m > 0.f ? m : __uint_as_float(*maxbits), n));
-    if (un.w) sym_unit<XT, true>(x, acc, scale, un, n, offset);
-    else sym_unit<XT, false>(x, acc, scale, un, n, offset);
+    if (un.w) sym_unit<XT, true, ABS>(x, acc, scale, un, n, offset);
+    else sym_unit<XT, false, ABS>(x, acc, scale, un, n, offset);
+}
+
+// u = the fixed-point sums as floats (clears them)
+__global__ void proc_sym_to_float(unsigned long long *__restrict__ acc, const unsigned *__restrict__ maxbits,
+                                  float *__restrict__ u, int64_t n) {
+    const double inv = ldexp(1.0, -fixed_exp(__uint_as_float(*maxbits), n));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        u[i] = static_cast<float>(static_cast<double>(static_cast<long long>(acc[i])) * inv);
+        acc[i] = 0ull;
+    }
+}
+
+// per block: max over rows of the fixed-point sums (FP64); clears them
+__global__ void __launch_bounds__(kQT)
+proc_sym_rowmax(unsigned long long *__restrict__ acc, int64_t n, double inv, double *__restrict__ bmax) {
+    double m = 0.0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kQT + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kQT) {
+        m = fmax(m, static_cast<double>(static_cast<long long>(acc[i])) * inv);
+        acc[i] = 0ull;
+    }
+    __shared__ double red[kQT];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = kQT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bmax[blockIdx.x] = red[0];
+}
+
+// u = sum of the split partials in split order
+__global__ void proc_sum_splits(const float *__restrict__ part, int S, float *__restrict__ u, int64_t count) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float v = part[e];
+        for (int s = 1; s < S; ++s) v += part[static_cast<int64_t>(s) * count + e];
+        u[e] = v;
+    }
 }
 
 // x_out = cbrt((u + alpha x) / beta) with u the fixed-point sums; clears them
@@ -639,18 +681,56 @@ ising_status_t proc_energy(ising_context *c, const void *x, int xtype, int R, do
     return ISING_OK;
 }
 
-// Eq. alphabeta with the Wigner estimate of Eq. estimate_eig_J
-ising_status_t proc_params(const ising_context *c, double eta, double *alpha, double *beta) {
-    const int rb = static_cast<int>((c->n + kPT - 1) / kPT);
-    const int nt = static_cast<int>((c->n + kPN - 1) / kPN);
+// u = J x (FP32, [n][R]), for the ADOCH passes
+ising_status_t proc_product(ising_context *c, const float *x, float *u, int R, cudaStream_t st) {
+    if (R == 1) {
+        DOCH_CHECK(sym_setup(c));
+        unsigned *mw = sym_maxword(c);
+        DOCH_CUDA(cudaMemsetAsync(mw, 0, sizeof(unsigned), st));
+        proc_maxabs<<<stream_blocks(c, c->n), 256, 0, st>>>(x, c->n, mw);
+        proc_sym<float><<<c->proc_units_count, kPT, 0, st>>>(x, c->proc_acc.as<unsigned long long>(), mw, 0.f,
+                                                           c->proc_units.as<int4>(), c->n, c->proc_offset);
+        proc_sym_to_float<<<stream_blocks(c, c->n), 256, 0, st>>>(c->proc_acc.as<unsigned long long>(), mw, u, c->n);
+        DOCH_CUDA(cudaGetLastError());
+        return ISING_OK;
+    }
+    const SplitPlan pl = plan_splits(c);
+    const int64_t count = c->n * R;
+    DOCH_CHECK(c->partials.ensure(sizeof(float) * count * pl.S));
+    float *part = c->partials.as<float>();
+    DOCH_CHECK(proc_products<float>(c, x, part, R, pl, st));
+    proc_sum_splits<<<stream_blocks(c, count), 256, 0, st>>>(part, pl.S, u, count);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+// H(x^k) of Eq. Hamilton per replica into H_out [R] (device): one product and an FP64 reduction
+ising_status_t proc_hamiltonian(ising_context *c, const float *x, int R, const ParamTabs &p, int k, double *H_out,
+                                cudaStream_t st) {
+    DOCH_CHECK(c->proc_u.ensure(sizeof(float) * c->n * R));
+    float *u = c->proc_u.as<float>();
+    DOCH_CHECK(proc_product(c, x, u, R, st));
+    proc_ham<<<R, kQT, 0, st>>>(x, u, c->n, R, p.alpha_d, p.alpha_len, k, p.beta_d, H_out);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+// Eq. alphabeta with the Wigner estimate of Eq. estimate_eig_J; the row sums
+// of |J_ij| by the symmetric product with |J| and all-ones x
+ising_status_t proc_params(ising_context *c, double eta, double *alpha, double *beta) {
+    DOCH_CHECK(sym_setup(c));
+    constexpr int kMB = 64;
     DevBuf b;
-    DOCH_CHECK(b.ensure(sizeof(double) * rb));
-    proc_rowabs<<<rb, kPT>>>(c->n, c->proc_offset, nt, b.as<double>());
+    DOCH_CHECK(b.ensure(sizeof(double) * kMB));
+    proc_sym<float, true><<<c->proc_units_count, kPT>>>(nullptr, c->proc_acc.as<unsigned long long>(), nullptr, 1.f,
+                                                       c->proc_units.as<int4>(), c->n, c->proc_offset);
+    proc_sym_rowmax<<<kMB, kQT>>>(c->proc_acc.as<unsigned long long>(), c->n, std::ldexp(1.0, -fixed_exp(1.f, c->n)),
+                                  b.as<double>());
     cudaError_t e = cudaGetLastError();
-    std::vector<double> h(rb);
-    if (e == cudaSuccess) e = cudaMemcpy(h.data(), b.ptr, sizeof(double) * rb, cudaMemcpyDeviceToHost);
+    std::vector<double> h(kMB);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), b.ptr, sizeof(double) * kMB, cudaMemcpyDeviceToHost);
     b.release();
-    if (e != cudaSuccess) return cuda_fail(e, "proc_rowabs");
+    if (e != cudaSuccess) return cuda_fail(e, "procedural row sums");
     const double rowmax = *std::max_element(h.begin(), h.end());
     const double n = static_cast<double>(c->n);
     const double cnt = n * (n - 1.0);

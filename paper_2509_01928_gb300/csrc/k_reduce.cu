@@ -320,6 +320,10 @@ ising_status_t energy_reduce(ising_context *c, const void *x, int xtype, int R, 
 
 ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, int R,
                                   const ParamTabs &p, int k, double *H_out, cudaStream_t st) {
+    if (c->format == ISING_FMT_PROCEDURAL) {
+        if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+        return proc_hamiltonian(c, static_cast<const float *>(x), R, p, k, H_out, st);
+    }
     const int chunks = pick_chunks(c, R);
     ising_status_t s;
     switch (xtype) {

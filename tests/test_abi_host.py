@@ -116,3 +116,80 @@ def test_default_params_batched(lib):
         ao, bo = O.alpha_beta(g, eta=1.0, method="eig")
         assert a[k] == pytest.approx(ao, rel=1e-6)
         assert b[k] == pytest.approx(bo, rel=1e-6)
+
+
+def test_problem_struct_layout_matches_the_header(tmp_path):
+    """The ctypes ising_problem_t of the binding has the size and field offsets
+    the C compiler gives the header's struct."""
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in N.IsingProblem._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ising.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(ising_problem_t));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof(ising_problem_t, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(N.IsingProblem)
+    assert out[1:] == [getattr(N.IsingProblem, f).offset for f in fields]
+
+
+class _Ell:
+    def __init__(self, csr, width, pad_first=False):
+        n = csr.n
+        self.ell_col = np.full((n, width), -1, np.int32)
+        self.ell_val = np.zeros((n, width), np.asarray(csr.val).dtype)
+        for i in range(n):
+            e0, e1 = csr.row_ptr[i], csr.row_ptr[i + 1]
+            k0 = width - (e1 - e0) if pad_first else 0
+            self.ell_col[i, k0:k0 + e1 - e0] = csr.col[e0:e1]
+            self.ell_val[i, k0:k0 + e1 - e0] = csr.val[e0:e1]
+
+
+def test_ell_input_is_the_csr_problem(lib):
+    """ELL rows (empty slots -1, anywhere in the row) load as the same CSR problem:
+    the same parameters by the power method, batched too; bad columns are rejected."""
+    g = I.regular_gauss(300, 5, seed=611)
+    for pad_first in (False, True):
+        a_csr, b_csr = N.ising_default_params(N.Problem(g), eta=1.0, method=1)
+        a_ell, b_ell = N.ising_default_params(N.Problem(_Ell(g, 8, pad_first)), eta=1.0, method=1)
+        assert np.array_equal(a_csr, a_ell) and np.array_equal(b_csr, b_ell)
+    gs = [I.regular_pm1(120, 3, seed=612), I.regular_pm1(80, 4, seed=613)]
+    off = np.array([0, 120, 200], np.int64)
+    rp = np.concatenate([[0], gs[0].row_ptr[1:], gs[1].row_ptr[1:] + gs[0].row_ptr[-1]])
+    col = np.concatenate([gs[0].col, gs[1].col + 120]).astype(np.int32)
+    J = I.CSR(200, rp, col, np.concatenate([gs[0].val, gs[1].val]))
+    a1, b1 = N.ising_default_params(N.Problem(J, instances=off), eta=1.0, method=1)
+    a2, b2 = N.ising_default_params(N.Problem(_Ell(J, 6), instances=off), eta=1.0, method=1)
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    bad = _Ell(g, 8)
+    bad.ell_col[3, 7] = 300
+    with pytest.raises(N.IsingError, match="INDEX_RANGE"):
+        N.ising_default_params(N.Problem(bad), eta=1.0, method=1)
+
+
+def test_dense_values_in_fp8_bf16_and_float_types(lib):
+    """Dense couplings may come in any storage type as long as they are integers with
+    |J| <= 256: FP8 E4M3 bytes (+1 = 0x38, -1 = 0xB8, 0 = 0x00, 2 = 0x40), BF16,
+    F32 give the parameters of the int8 matrix; a non-integer is rejected."""
+    Jd = I.dense_pm1(64, seed=614).astype(np.int8)
+    Jd[3, 5] = Jd[5, 3] = 2
+    ref = N.ising_default_params(N.Problem(Jd), eta=1.0, method=1)
+    codes = {1: 0x38, -1: 0xB8, 0: 0x00, 2: 0x40}
+    fp8 = np.vectorize(lambda v: codes[int(v)])(Jd).astype(np.uint8)
+    got = N.ising_default_params(N.Problem(fp8, jtype=N.FP8E4M3), eta=1.0, method=1)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    bf16 = (Jd.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    got = N.ising_default_params(N.Problem(bf16, jtype=N.BF16), eta=1.0, method=1)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    got = N.ising_default_params(N.Problem(Jd.astype(np.float32)), eta=1.0, method=1)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    half = Jd.astype(np.float32)
+    half[1, 2] = half[2, 1] = 0.5
+    with pytest.raises(N.IsingError, match="UNSUPPORTED"):
+        N.ising_default_params(N.Problem(half), eta=1.0, method=1)

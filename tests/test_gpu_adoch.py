@@ -172,7 +172,7 @@ def test_adoch_rejects_dense():
     hd = N.ising_create(N.Problem(J))
     try:
         x = torch.zeros((64, 2), dtype=torch.float32, device="cuda")
-        with pytest.raises(N.IsingError, match="ADOCH runs on CSR or TORUS2D"):
+        with pytest.raises(N.IsingError, match="ADOCH runs on CSR, TORUS2D or PROCEDURAL"):
             N.ising_iterate_adoch(hd, x, [1.0], [1.0], 3, 2)
     finally:
         N.ising_destroy(hd)

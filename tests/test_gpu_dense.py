@@ -148,3 +148,27 @@ def test_dense_full_size_16384x256_sampled():
         assert _rel(x.float().cpu().numpy()[:, sample].astype(np.float64), ref5).max() <= TOL_BF16
     finally:
         N.ising_destroy(h)
+
+
+def test_dense_fp8_input_is_the_int8_problem():
+    """J given as FP8 E4M3 bytes (+1 = 0x38, -1 = 0xB8, 0 = 0x00, 2 = 0x40, 3 = 0x44) creates the
+    same device problem as the int8 matrix: identical iterates and exact energies."""
+    n, R = 200, 20
+    for kind in ("pm1", "int"):
+        J = _jmat(kind, n, 97)
+        codes = {1: 0x38, -1: 0xB8, 0: 0x00, 2: 0x40, -2: 0xC0, 3: 0x44, -3: 0xC4}
+        J8 = np.vectorize(lambda v: codes[int(v)])(J).astype(np.uint8)
+        alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+        xt, _ = _bf16(I.x0_uniform(n, R, seed=98))
+        outs = []
+        for prob in (N.Problem(J), N.Problem(J8, jtype=N.FP8E4M3)):
+            h = N.ising_create(prob)
+            try:
+                x = xt.cuda()
+                N.ising_iterate(h, x, [alpha], [beta], 12)
+                E = np.zeros(R, np.int64)
+                N.ising_energy(h, x, E_int=E)
+                outs.append((x.float().cpu().numpy(), E))
+            finally:
+                N.ising_destroy(h)
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

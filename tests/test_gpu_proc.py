@@ -97,6 +97,34 @@ def test_proc_schedule_matches_oracle():
         N.ising_destroy(hd)
 
 
+@pytest.mark.parametrize("n,R", [(1500, 1), (1100, 3)])
+def test_proc_hamiltonian_trace(n, R):
+    """H(x^k) of Eq. Hamilton along the device iterates: each value against the oracle's H of the
+    device's own iterate (FP64 sums, 1e-9), and non-increasing for alpha >= lambda_max(-J)."""
+    J = I.procedural_sin(n, C)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    x0 = I.x0_uniform(n, R, seed=480 + n)
+    iters = 12
+    hd = N.ising_create_procedural(n, C)
+    try:
+        x = torch.from_numpy(x0.copy()).cuda()
+        H = np.zeros((iters + 1, R))
+        N.ising_iterate(hd, x, [alpha], [beta], iters, H_trace=H)
+        xs = [x0.copy()]
+        xk = torch.from_numpy(x0.copy()).cuda()
+        for _ in range(iters):
+            N.ising_iterate(hd, xk, [alpha], [beta], 1)
+            xs.append(xk.cpu().numpy())
+    finally:
+        N.ising_destroy(hd)
+    P = O.Problem(J)
+    for k in (0, 1, 5, iters):
+        Href = O.hamiltonian(P, xs[k].astype(np.float64), alpha, beta)
+        # the device's u = J x carries the FP32 product error (~1e-6 relative): H to 1e-5 of its scale
+        assert np.all(np.abs(H[k] - Href) <= 1e-5 * np.abs(Href).max())
+    assert np.all(H[1:] <= H[:-1] + 1e-6 * np.abs(H[:-1]))
+
+
 @pytest.mark.parametrize("n,R", [(1000, 5), (2560, 1), (4097, 1), (300, 17)])
 def test_proc_energy_matches_oracle(n, R):
     J = I.procedural_sin(n, C)
@@ -245,11 +273,41 @@ def test_proc_rejects():
         with pytest.raises(N.IsingError, match="PROCEDURAL iterates are F32"):
             N.ising_iterate(hd, x, [1.0], [1.0], 1)
         xf = torch.zeros((64, 2), dtype=torch.float32, device="cuda")
-        with pytest.raises(N.IsingError, match="H trace"):
-            N.ising_iterate(hd, xf, [1.0], [1.0], 2, H_trace=np.zeros((3, 2)))
-        with pytest.raises(N.IsingError):
-            N.ising_iterate_adoch(hd, xf, [1.0], [1.0], 2, 1)
+        with pytest.raises(N.IsingError, match="PROCEDURAL iterates are F32"):
+            N.ising_iterate_adoch(hd, x, [1.0], [1.0], 2, 1)
         with pytest.raises(N.IsingError):
             N.ising_energy(hd, xf, E_int=np.zeros(2, np.int64))
+    finally:
+        N.ising_destroy(hd)
+
+
+@pytest.mark.parametrize("n,R,q", [(1500, 1, 1), (1200, 3, 5), (3000, 1, 3)])
+def test_proc_adoch(n, R, q):
+    """ADOCH (Algorithm 2) on the procedural couplings: the first steps against the oracle
+    replaying the device's decisions (1e-5, while the trajectory is well conditioned), every
+    decision whose margin is clear on that stretch, and H(x^k) of a longer q = 0 run never
+    rising (each accepted point is no worse than x^k and the DOCH step descends)."""
+    J = I.procedural_sin(n, C)
+    P = O.Problem(J)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")  # alpha >= lambda_max(-J): g convex, T descends
+    x0 = I.x0_uniform(n, R, seed=470 + n)
+    hd = N.ising_create_procedural(n, C)
+    try:
+        for iters in (1, 2, 3):
+            x = torch.from_numpy(x0.copy()).cuda()
+            acc = torch.zeros((iters, R), dtype=torch.int8, device="cuda")
+            N.ising_iterate_adoch(hd, x, [alpha], [beta], iters, q, accepted=acc)
+            acc = acc.cpu().numpy()
+            ref, _, m = O.adoch(P, x0.astype(np.float64), alpha, beta, iters, q, decisions=acc, margins=True)
+            assert _rel(x.cpu().numpy(), ref).max() <= 1e-5
+            clear = np.abs(m) > 1e-4
+            np.testing.assert_array_equal(acc[clear], (m[clear] >= 0).astype(np.int8))
+        iters = 40
+        x = torch.from_numpy(x0.copy()).cuda()
+        H = torch.zeros((iters + 1, R), dtype=torch.float64, device="cuda")
+        N.ising_iterate_adoch(hd, x, [alpha], [beta], iters, 0, H_trace=H)
+        H = H.cpu().numpy()
+        assert np.all(H[1:] <= H[:-1] + 1e-6 * np.abs(H[:-1]))
+        assert np.all(H[-1] < H[0])
     finally:
         N.ising_destroy(hd)
