@@ -771,7 +771,8 @@ class Proc:
                                    f"+ sign + FP64 energy",
                        "n": self.n, "replicas": self.R, "iters": self.iters,
                        "create_ms": 1e3 * (t1 - t0), "params_ms": 1e3 * (t2 - t1),
-                       "l2": "compute bound; the iterate (4 MB) is L2-resident; no flush",
+                       "l2": f"compute bound; the iterate ({self.n * self.R * 4 / 1e6:.0f} MB) is L2-resident; "
+                             "no flush",
                        "alpha_beta": "Wigner estimate on the device, eta = 1, beta of Eq. alphabeta"}
 
     def step(self, sid, stream, ev_a=None, ev_b=None):
