@@ -64,6 +64,8 @@ __device__ __forceinline__ void stv(T *p, const T (&v)[V]) {
     *reinterpret_cast<VT *>(p) = w;
 }
 
+constexpr int kCsrBatch = 8;  // entries whose loads are issued together
+
 template <typename XT, typename VT, int V>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
@@ -87,7 +89,26 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
 #pragma unroll
         for (int q = 0; q < V; ++q) acc[q] = XT(0);
         const int64_t e1 = __ldg(row_ptr + i + 1);
-        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
+        int64_t e = __ldg(row_ptr + i);
+        // entries in batches of kCsrBatch: the index/value loads first, then the gathers, then
+        // the products in entry order (the same sums as one entry at a time)
+        for (; e + kCsrBatch <= e1; e += kCsrBatch) {
+            int32_t js[kCsrBatch];
+            XT ws[kCsrBatch];
+#pragma unroll
+            for (int t = 0; t < kCsrBatch; ++t) {
+                js[t] = __ldg(col + e + t);
+                ws[t] = static_cast<XT>(__ldg(val + e + t));
+            }
+            XT xv[kCsrBatch][V];
+#pragma unroll
+            for (int t = 0; t < kCsrBatch; ++t) ldv<XT, V>(xi + static_cast<int64_t>(js[t]) * R + ch * V, xv[t]);
+#pragma unroll
+            for (int t = 0; t < kCsrBatch; ++t)
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] += ws[t] * xv[t][q];
+        }
+        for (; e < e1; ++e) {
             const int64_t j = __ldg(col + e);
             const XT w = static_cast<XT>(__ldg(val + e));
             XT xv[V];
