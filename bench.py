@@ -142,6 +142,25 @@ def cpu_oracle_sample(lr: int, lc: int, iters: int):
     return t.n * iters, dt
 
 
+def _oracle_sample_task(a):
+    return cpu_oracle_sample(*a)
+
+
+def oracle_x_cores(lr: int, lc: int, iters: int):
+    """The same oracle sample run as P independent single-threaded processes (one per host core,
+    started with spawn), each on its own copy of the sample: an embarrassingly parallel baseline."""
+    import multiprocessing as mp
+    P = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(P) as pool:
+        pool.map(_oracle_sample_task, [(64, 64, 2)] * P)  # start-up and library load, untimed
+        w0 = time.perf_counter()
+        res = pool.map(_oracle_sample_task, [(lr, lc, iters)] * P)
+        wall = time.perf_counter() - w0
+    return {"value": sum(u for u, _ in res) / wall, "unit": UNIT, "cores": P, "kind": "oracle x cores",
+            "sample": f"{P} processes, each torus {lr}x{lc}, {iters} FP64 DOCH iterations + sign + int64 energy"}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -166,6 +185,7 @@ def run_reference(args):
                    "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_x_cores": oracle_x_cores(lr, lc, iters),
     }
     print(json.dumps(line), flush=True)
 
