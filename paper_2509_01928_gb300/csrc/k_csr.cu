@@ -11,6 +11,8 @@
 // shared memory. One CTA per (instance, replica) keeps that replica's
 // iterate in two shared-memory buffers and separates the steps with
 // __syncthreads(); the CSR arrays stream through L1/L2.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace doch {
@@ -162,6 +164,75 @@ csr_fused_kernel(XT *__restrict__ x, const int64_t *__restrict__ row_ptr,
     for (int i = threadIdx.x; i < nb; i += blockDim.x) x[(lo + i) * R + r] = cur[i];
 }
 
+// Small instances over a cluster of K CTAs per (instance b = blockIdx.y, replica r = blockIdx.x / K):
+// every CTA keeps both copies of the pair's whole iterate, computes the rows of its share
+// [q c, (q+1) c) (c = ceil(n_b / K), q its rank in the cluster) with the arithmetic of
+// csr_fused_kernel, and stores each new value into the next copy of all K CTAs (distributed
+// shared memory); a cluster barrier ends each step. The same iterates as one CTA per pair, with
+// the FP64 arithmetic of a pair spread over K SMs.
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cl_store(uint32_t a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cl_store(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+template <typename XT, typename VT>
+__global__ void __launch_bounds__(1024)
+csr_fused_cluster(XT *__restrict__ x, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                  const VT *__restrict__ val, const XT *__restrict__ h, const int64_t *__restrict__ inst_off,
+                  int64_t n, int R, const double *__restrict__ alpha_tab, int alpha_len,
+                  const double *__restrict__ beta_tab, int iters, int K) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    XT *buf = reinterpret_cast<XT *>(smem_raw);
+    const uint32_t q = cl_rank();
+    const int b = blockIdx.y, r = blockIdx.x / K;
+    const int64_t lo = inst_off ? inst_off[b] : 0;
+    const int64_t hi = inst_off ? inst_off[b + 1] : n;
+    const int nb = static_cast<int>(hi - lo);
+    const int chunk = (nb + K - 1) / K;
+    const int i0 = min(nb, static_cast<int>(q) * chunk), i1 = min(nb, i0 + chunk);
+    XT *cur = buf, *nxt = buf + nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = x[(lo + i) * R + r];
+    const XT bb = static_cast<XT>(beta_tab[b]);
+    cl_sync();  // every CTA of the cluster runs, and has loaded, before the first remote store
+    for (int k = 0; k < iters; ++k) {
+        const XT a = static_cast<XT>(alpha_tab[static_cast<int64_t>(b) * alpha_len + (alpha_len == 1 ? 0 : k)]);
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int64_t row = lo + i;
+            XT acc = XT(0);
+            const int64_t e1 = __ldg(row_ptr + row + 1);
+            for (int64_t e = __ldg(row_ptr + row); e < e1; ++e)
+                acc += static_cast<XT>(__ldg(val + e)) * cur[__ldg(col + e) - lo];
+            const XT hv = h ? h[row] : XT(0);
+            const XT v = dcbrt((acc + a * cur[i] + hv) / bb);
+            nxt[i] = v;
+            for (int t = 0; t < K; ++t)
+                if (t != static_cast<int>(q)) cl_store(cl_map(nxt + i, static_cast<uint32_t>(t)), v);
+        }
+        cl_sync();  // the new values of every share are in every CTA; the old copy is free
+        XT *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) x[(lo + i) * R + r] = cur[i];
+}
+
 template <typename XT, typename VT, int V>
 void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
                  const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, cudaStream_t st) {
@@ -193,9 +264,54 @@ ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R,
     return ISING_OK;
 }
 
+// the cluster size for the fused kernel: the largest K in {8, 4, 2} that leaves each CTA at least
+// 64 rows and keeps all pairs' clusters within the SMs; 1 when none does
+int fused_cluster_k(const ising_context *c, int R) {
+    for (int K = 8; K >= 2; K >>= 1)
+        if (static_cast<int64_t>(c->n_inst) * R * K <= c->num_sms && c->max_inst_n >= 64LL * K) return K;
+    return 1;
+}
+
+template <typename XT, typename VT>
+ising_status_t launch_fused_cluster(const ising_context *c, XT *x, int R, const XT *h, const ParamTabs &p,
+                                    int iters, int K, cudaStream_t st) {
+    const size_t smem = 2 * static_cast<size_t>(c->max_inst_n) * sizeof(XT);
+    auto kern = csr_fused_cluster<XT, VT>;
+    DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    const int64_t chunk = (c->max_inst_n + K - 1) / K;
+    int threads = static_cast<int>(std::min<int64_t>(1024, (chunk + 31) / 32 * 32));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(K);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(R * K), static_cast<unsigned>(c->n_inst));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return ISING_ERR_UNSUPPORTED;
+    }
+    DOCH_CUDA(cudaLaunchKernelEx(&cfg, kern, x, static_cast<const int64_t *>(c->row_ptr),
+                                 static_cast<const int32_t *>(c->col), static_cast<const VT *>(c->val), h,
+                                 static_cast<const int64_t *>(c->n_inst > 1 ? c->inst_off : nullptr), c->n, R,
+                                 p.alpha_d, p.alpha_len, p.beta_d, iters, K));
+    return ISING_OK;
+}
+
 template <typename XT, typename VT>
 ising_status_t launch_fused(const ising_context *c, XT *x, int R, const XT *h,
                             const ParamTabs &p, int iters, cudaStream_t st) {
+    const int K = fused_cluster_k(c, R);
+    if (K > 1) {
+        const ising_status_t s = launch_fused_cluster<XT, VT>(c, x, R, h, p, iters, K, st);
+        if (s != ISING_ERR_UNSUPPORTED) return s;
+    }
     const size_t smem = 2 * static_cast<size_t>(c->max_inst_n) * sizeof(XT);
     auto kern = csr_fused_kernel<XT, VT>;
     DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
