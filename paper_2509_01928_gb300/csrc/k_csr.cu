@@ -264,11 +264,11 @@ ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R,
     return ISING_OK;
 }
 
-// the cluster size for the fused kernel: the largest K in {8, 4, 2} that leaves each CTA at least
-// 64 rows and keeps all pairs' clusters within the SMs; 1 when none does
-int fused_cluster_k(const ising_context *c, int R) {
-    for (int K = 8; K >= 2; K >>= 1)
-        if (static_cast<int64_t>(c->n_inst) * R * K <= c->num_sms && c->max_inst_n >= 64LL * K) return K;
+// the cluster size for the fused kernel: the largest K in {16, 8, 4, 2} (16 is a non-portable size)
+// that leaves each CTA at least 32 rows and keeps all pairs' clusters within the SMs; 1 when none does
+int fused_cluster_k(const ising_context *c, int R, int kmax) {
+    for (int K = kmax; K >= 2; K >>= 1)
+        if (static_cast<int64_t>(c->n_inst) * R * K <= c->num_sms && c->max_inst_n >= 32LL * K) return K;
     return 1;
 }
 
@@ -278,6 +278,10 @@ ising_status_t launch_fused_cluster(const ising_context *c, XT *x, int R, const 
     const size_t smem = 2 * static_cast<size_t>(c->max_inst_n) * sizeof(XT);
     auto kern = csr_fused_cluster<XT, VT>;
     DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    if (K > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_UNSUPPORTED;
+    }
     const int64_t chunk = (c->max_inst_n + K - 1) / K;
     int threads = static_cast<int>(std::min<int64_t>(1024, (chunk + 31) / 32 * 32));
     cudaLaunchConfig_t cfg = {};
@@ -307,10 +311,12 @@ ising_status_t launch_fused_cluster(const ising_context *c, XT *x, int R, const 
 template <typename XT, typename VT>
 ising_status_t launch_fused(const ising_context *c, XT *x, int R, const XT *h,
                             const ParamTabs &p, int iters, cudaStream_t st) {
-    const int K = fused_cluster_k(c, R);
-    if (K > 1) {
+    for (int kmax = 16; kmax >= 2; kmax >>= 1) {
+        const int K = fused_cluster_k(c, R, kmax);
+        if (K < 2) break;
         const ising_status_t s = launch_fused_cluster<XT, VT>(c, x, R, h, p, iters, K, st);
         if (s != ISING_ERR_UNSUPPORTED) return s;
+        kmax = K;  // this size is not available: try the next smaller one
     }
     const size_t smem = 2 * static_cast<size_t>(c->max_inst_n) * sizeof(XT);
     auto kern = csr_fused_kernel<XT, VT>;
