@@ -603,7 +603,7 @@ class Er800:
 class Adoch:
     """ADOCH (Algorithm 2) on the 10^4 x 10^4 lattice, FP32, R = 1, q = 5, 100 steps per timed step."""
 
-    dominant = "adoch step (adoch_lattice<false> + adoch_decide + adoch_lattice<true>)"
+    dominant = "adoch step (adoch_lattice<2> + adoch_lattice_bound + adoch_decide)"
     dtype = "f32"
 
     def __init__(self, args, rank, N, I, torch):
@@ -641,9 +641,10 @@ class Adoch:
 
     def roofline(self, per_launch_s):
         peak, kind = measured_peaks()
-        # per step and site: the pass reads x^k, x^(k-1) and the couplings (10 B); the update reads
-        # them again and writes x^(k+1) (14 B); both coupling products are recomputed, not stored
-        alg = 24 * self.n
+        # per step and site: one pass reads x^k, x^(k-1) and the couplings (10 B) and writes x^(k+1)
+        # (4 B), forming from the new values the H terms of the next step (plus an edge pass over
+        # the ~1 % of sites on warp and strip boundaries, not counted)
+        alg = 14 * self.n
         ach = alg / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "kernel": self.dominant, "peak_kind": kind,

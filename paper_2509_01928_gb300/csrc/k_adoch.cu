@@ -18,6 +18,7 @@
 // FP32 iterates each thread first sums its sites' terms in FP32 with Kahan
 // compensation (FP64 arithmetic is a small fraction of the FP32 rate here),
 // with FP64 iterates in FP64.
+#include <algorithm>
 #include <cmath>
 #include <utility>
 
@@ -268,12 +269,17 @@ __device__ __forceinline__ float lat_sum(float wr, float xr, float wl, float xl,
     return wr * xr + wl * xl + wd * xd + wu * xu;
 }
 
-template <bool UPDATE>
+// MODE 0: pass (H terms of step k); 1: update x^(k+1); 2: update and, from the new values, the H
+// terms of step k+1 (x^T J x as twice the sum over right and down edges; the right edges of the
+// last column of a warp and the down edges of the last row of a strip are left to
+// adoch_lattice_bound)
+template <int MODE>
 __global__ void __launch_bounds__(kAThreads, 3)
 adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float *__restrict__ x2,
               const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc, int tiles, int bpt,
-              float c, const float *__restrict__ alpha_tab, const float *__restrict__ zs_tab,
+              float c, float c_next, const float *__restrict__ alpha_tab, const float *__restrict__ zs_tab,
               const float *__restrict__ xsc_tab, const int *__restrict__ dec, double *__restrict__ partials) {
+    constexpr bool UPDATE = MODE != 0;
     const int tile = blockIdx.x % tiles;
     const int part = blockIdx.x / tiles;
     const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
@@ -319,6 +325,7 @@ adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float 
         int dm = ldw(down, o), rt = ldw(right, o);
         float wl_h = is_l ? static_cast<float>(__ldg(right + hcol + o)) : 0.f;
         float ahd = ldh(x1, od), bhd = ldh(x0, od);
+        float pxn[4] = {0.f, 0.f, 0.f, 0.f}, pyn[4] = {0.f, 0.f, 0.f, 0.f};  // new values of the row above (MODE 2)
         for (int r = r0; r < r1; ++r) {
             const int64_t onn = od + Lc == n ? 0 : od + Lc;
             // loads of the next row, one row ahead
@@ -380,7 +387,43 @@ adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float 
                     rs[5] += y * jy;
                 }
             }
-            if (!UPDATE) {
+            if (MODE == 2) {
+                float yn[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    yn[q] = out[q] + c_next * (out[q] - am_[q]);
+                    const float x2v = out[q] * out[q], y2 = yn[q] * yn[q];
+                    rs[0] += x2v * x2v;
+                    rs[1] += x2v;
+                    rs[3] += y2 * y2;
+                    rs[4] += y2;
+                }
+                // right edges of this row (the lane to the right holds the next four columns)
+                const float xr_n = __shfl_down_sync(kFullMask, out[0], 1);
+                const float yr_n = __shfl_down_sync(kFullMask, yn[0], 1);
+                float ex = wr[0] * out[0] * out[1] + wr[1] * out[1] * out[2] + wr[2] * out[2] * out[3];
+                float ey = wr[0] * yn[0] * yn[1] + wr[1] * yn[1] * yn[2] + wr[2] * yn[2] * yn[3];
+                if (!is_r) {
+                    ex += wr[3] * out[3] * xr_n;
+                    ey += wr[3] * yn[3] * yr_n;
+                }
+                // down edges of the row above (its new values kept from the last pass of the walk)
+                if (r > r0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        ex += du[q] * pxn[q] * out[q];
+                        ey += du[q] * pyn[q] * yn[q];
+                    }
+                }
+                rs[2] = 2.f * ex;
+                rs[5] = 2.f * ey;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    pxn[q] = out[q];
+                    pyn[q] = yn[q];
+                }
+            }
+            if (MODE != 1) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) add(k, rs[k]);
             }
@@ -404,7 +447,7 @@ adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float 
             od = onn;
         }
     }
-    if (UPDATE) return;
+    if (MODE == 1) return;
     // block sums in FP64 in a fixed order; inactive lanes (wrapped columns) add nothing
     __shared__ double red[kAThreads / 32][kTerms];
     const int warp = threadIdx.x >> 5;
@@ -426,13 +469,66 @@ adoch_lattice(const float *__restrict__ x1, const float *__restrict__ x0, float 
     }
 }
 
+// The edges adoch_lattice<2> leaves out: the right edge of every column c = 128 m + 127 (the last
+// column of a warp) in every row, and the down edge of the last row of every strip, each adding
+// 2 J x_i x_j of x^(k+1) and of y^(k+1) = x^(k+1) + c_next (x^(k+1) - x^k) to the H terms of step k+1.
+__global__ void __launch_bounds__(kAThreads)
+adoch_lattice_bound(const float *__restrict__ x1, const float *__restrict__ x2, const int8_t *__restrict__ right,
+                    const int8_t *__restrict__ down, int Lr, int Lc, int bpt, float c_next,
+                    double *__restrict__ partials) {
+    const int nvb = Lc / 128;
+    const int64_t nv = static_cast<int64_t>(Lr) * nvb;
+    const int64_t total = nv + static_cast<int64_t>(bpt) * Lc;
+    float ex = 0.f, ey = 0.f;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * kAThreads + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * kAThreads) {
+        int64_t a, b;
+        float w;
+        if (idx < nv) {
+            const int64_t r = idx / nvb;
+            const int64_t cc = (idx - r * nvb) * 128 + 127;
+            const int64_t cn = cc + 1 == Lc ? 0 : cc + 1;
+            a = r * Lc + cc;
+            b = r * Lc + cn;
+            w = static_cast<float>(right[a]);
+        } else {
+            const int64_t t = idx - nv;
+            const int64_t p = t / Lc;
+            const int64_t cc = t - p * Lc;
+            const int64_t r = static_cast<int64_t>(Lr) * (p + 1) / bpt - 1;
+            const int64_t rn = r + 1 == Lr ? 0 : r + 1;
+            a = r * Lc + cc;
+            b = rn * Lc + cc;
+            w = static_cast<float>(down[a]);
+        }
+        const float xa = x2[a], xb = x2[b];
+        const float ya = xa + c_next * (xa - x1[a]), yb = xb + c_next * (xb - x1[b]);
+        ex += w * xa * xb;
+        ey += w * ya * yb;
+    }
+    __shared__ double red[kAThreads / 32][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double vx = warp_sum(2.0 * static_cast<double>(ex)), vy = warp_sum(2.0 * static_cast<double>(ey));
+    if (lane == 0) {
+        red[warp][0] = vx;
+        red[warp][1] = vy;
+    }
+    __syncthreads();
+    if (threadIdx.x < kTerms) {
+        double t = 0.0;
+        if (threadIdx.x == 2 || threadIdx.x == 6)
+            for (int w = 0; w < kAThreads / 32; ++w) t += red[w][threadIdx.x == 2 ? 0 : 1];
+        partials[static_cast<int64_t>(blockIdx.x) * kTerms + threadIdx.x] = t;
+    }
+}
+
 struct LatticeShape {
     int tiles = 0, bpt = 0, blocks = 0;
 };
 
 LatticeShape lattice_shape(const ising_context *c) {
     static int occ = 0;
-    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adoch_lattice<true>, kAThreads, 0) !=
+    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adoch_lattice<2>, kAThreads, 0) !=
                      cudaSuccess || occ < 1))
         occ = 1;
     LatticeShape s;
@@ -455,9 +551,13 @@ ising_status_t adoch_lattice_run(ising_context *c, float *x, const ParamTabs &p,
                                  double *H_dev, cudaStream_t st) {
     const int64_t count = c->n;
     const LatticeShape sh = lattice_shape(c);
+    const int Lr = static_cast<int>(c->l_rows), Lc = static_cast<int>(c->l_cols);
+    const int64_t bound_edges = static_cast<int64_t>(Lr) * (Lc / 128) + static_cast<int64_t>(sh.bpt) * Lc;
+    const int nbb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((bound_edges + kAThreads - 1) / kAThreads,
+                                                                             2LL * c->num_sms)));
     auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
     const size_t xb = al(sizeof(float) * count);
-    const size_t pb = al(sizeof(double) * static_cast<size_t>(sh.blocks) * kTerms);
+    const size_t pb = al(sizeof(double) * static_cast<size_t>(sh.blocks + nbb) * kTerms);
     const size_t hb = al(sizeof(double) * static_cast<size_t>(q + 1));
     const size_t db = al(sizeof(int));
     DOCH_CHECK(c->ckpt.ensure(2 * xb + pb + hb + db));
@@ -467,26 +567,44 @@ ising_status_t adoch_lattice_run(ising_context *c, float *x, const ParamTabs &p,
     double *hist = reinterpret_cast<double *>(base + 2 * xb + pb);
     int *dec = reinterpret_cast<int *>(base + 2 * xb + pb + hb);
     DOCH_CUDA(cudaMemcpyAsync(x0, x1, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));  // x^{-1} := x^0
-    const int Lr = static_cast<int>(c->l_rows), Lc = static_cast<int>(c->l_cols);
-    double t = 1.0;
+    if (iters <= 0) return ISING_OK;
+    // step 0: its H terms from a pass (y^0 = x^0)
+    adoch_lattice<0><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, nullptr, c->right, c->down, Lr, Lc, sh.tiles, sh.bpt,
+                                                     0.f, 0.f, nullptr, nullptr, nullptr, nullptr, part);
+    DOCH_CUDA(cudaGetLastError());
+    adoch_decide<<<1, kDThreads, 0, st>>>(part, 1, 1, sh.blocks, p.alpha_d, p.beta_d, 0, q, hist, dec, acc_dev, H_dev);
+    DOCH_CUDA(cudaGetLastError());
+    auto t_after = [](double t) { return (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0; };
+    double t = 1.0;  // t_k
     for (int k = 0; k < iters; ++k) {
-        const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
-        const float ck = static_cast<float>(k >= 1 ? (t - 1.0) / t_next : 0.0);
-        adoch_lattice<false><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, nullptr, c->right, c->down, Lr, Lc, sh.tiles,
-                                                            sh.bpt, ck, nullptr, nullptr, nullptr, nullptr, part);
-        DOCH_CUDA(cudaGetLastError());
-        adoch_decide<<<1, kDThreads, 0, st>>>(part, 1, 1, sh.blocks, p.alpha_d, p.beta_d, k, q, hist, dec, acc_dev,
-                                              H_dev);
-        DOCH_CUDA(cudaGetLastError());
-        adoch_lattice<true><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, x2, c->right, c->down, Lr, Lc, sh.tiles,
-                                                           sh.bpt, ck, p.alpha_f, p.zscale_f, p.xscale_f, dec,
-                                                           nullptr);
-        DOCH_CUDA(cudaGetLastError());
+        const double t1 = t_after(t), t2 = t_after(t1);  // t_(k+1), t_(k+2)
+        const float ck = static_cast<float>(k >= 1 ? (t - 1.0) / t1 : 0.0);
+        const float cn = static_cast<float>((t1 - 1.0) / t2);  // c_(k+1)
+        if (k + 1 < iters) {
+            // x^(k+1) and, from it, the H terms of step k+1
+            adoch_lattice<2><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, x2, c->right, c->down, Lr, Lc, sh.tiles,
+                                                             sh.bpt, ck, cn, p.alpha_f, p.zscale_f, p.xscale_f, dec,
+                                                             part);
+            DOCH_CUDA(cudaGetLastError());
+            adoch_lattice_bound<<<nbb, kAThreads, 0, st>>>(x1, x2, c->right, c->down, Lr, Lc, sh.bpt, cn,
+                                                          part + static_cast<size_t>(sh.blocks) * kTerms);
+            DOCH_CUDA(cudaGetLastError());
+        } else {
+            adoch_lattice<1><<<sh.blocks, kAThreads, 0, st>>>(x1, x0, x2, c->right, c->down, Lr, Lc, sh.tiles,
+                                                             sh.bpt, ck, 0.f, p.alpha_f, p.zscale_f, p.xscale_f, dec,
+                                                             nullptr);
+            DOCH_CUDA(cudaGetLastError());
+        }
         float *tx = x0;  // x^{k-1} <- x^k <- x^{k+1}
         x0 = x1;
         x1 = x2;
         x2 = tx;
-        t = t_next;
+        t = t1;
+        if (k + 1 < iters) {
+            adoch_decide<<<1, kDThreads, 0, st>>>(part, 1, 1, sh.blocks + nbb, p.alpha_d, p.beta_d, k + 1, q, hist,
+                                                  dec, acc_dev, H_dev);
+            DOCH_CUDA(cudaGetLastError());
+        }
     }
     if (x1 != x) DOCH_CUDA(cudaMemcpyAsync(x, x1, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));
     return ISING_OK;

@@ -128,11 +128,16 @@ def test_adoch_lattice_fp32(shape, q):
         xs = buf[1:].view(J.n, 1)
         xs.copy_(torch.from_numpy(x0))
         acc2 = torch.zeros((iters, 1), dtype=torch.int8, device="cuda")
-        N.ising_iterate_adoch(hd, xs, [alpha], [beta], iters, q, accepted=acc2)
-        x2, a2 = xs.cpu().numpy(), acc2.cpu().numpy()
+        H2 = torch.zeros((iters + 1, 1), dtype=torch.float64, device="cuda")
+        N.ising_iterate_adoch(hd, xs, [alpha], [beta], iters, q, accepted=acc2, H_trace=H2)
+        x2, a2, H2 = xs.cpu().numpy(), acc2.cpu().numpy(), H2.cpu().numpy()
     finally:
         N.ising_destroy(hd)
     _check(P, x0.astype(np.float64), alpha, beta, iters, q, x2, a2, None, 1e-5, 1e-4)
+    # H(x^k) of the two paths (the fast path forms x^T J x from edge sums of the new iterate) while
+    # their trajectories agree: the first ten steps, before the decisions near ties
+    np.testing.assert_allclose(H[:10], H2[:10], rtol=1e-5)
+    assert np.all(H[1:10] <= H[:9] + 1e-6 * np.abs(H[:9])) or q > 0
 
 
 def test_adoch_q0_never_rises():
