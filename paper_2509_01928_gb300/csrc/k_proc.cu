@@ -552,7 +552,14 @@ ising_status_t sym_setup(ising_context *c) {
     if (c->proc_units_count > 0) return ISING_OK;
     const int64_t n = c->n;
     const int64_t rt = (n + kSTR - 1) / kSTR, ct = (n + kSTC - 1) / kSTC;
+    int64_t total = rt;  // counted before anything is allocated
+    for (int64_t I = 0; I < rt; ++I) {
+        const int64_t first = (I + 1) * (kSTR / kSTC);
+        if (first < ct) total += (ct - first + kSUnit - 1) / kSUnit;
+    }
+    if (total > 0x7FFFFFFF) return fail(ISING_ERR_UNSUPPORTED, "procedural product: too many work units");
     std::vector<int4> u;
+    u.reserve(static_cast<size_t>(total));
     for (int64_t I = 0; I < rt; ++I) u.push_back(make_int4(static_cast<int>(I), 0, 0, 1));
     for (int64_t I = 0; I < rt; ++I) {
         const int64_t first = (I + 1) * (kSTR / kSTC);
@@ -560,7 +567,6 @@ ising_status_t sym_setup(ising_context *c) {
             u.push_back(make_int4(static_cast<int>(I), static_cast<int>(t),
                                   static_cast<int>(std::min<int64_t>(kSUnit, ct - t)), 0));
     }
-    if (u.size() > 0x7FFFFFFFu) return fail(ISING_ERR_UNSUPPORTED, "procedural product: too many work units");
     DOCH_CHECK(c->proc_units.ensure(sizeof(int4) * u.size()));
     DOCH_CUDA(cudaMemcpy(c->proc_units.ptr, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice));
     DOCH_CHECK(c->proc_acc.ensure(sizeof(unsigned long long) * n + 256));
