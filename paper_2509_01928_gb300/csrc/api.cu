@@ -816,602 +816,628 @@ const char *ising_last_error(void) { return g_err.c_str(); }
 
 ising_status_t ising_default_params(const ising_problem_t *p, double eta, int32_t method,
                                     double *alpha_out, double *beta_out) {
-    g_err.clear();
-    if (!alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "output pointers are NULL");
-    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
-    if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
-    HostProblem hp;
-    DOCH_CHECK(load_problem(p, true, hp));
-    for (int b = 0; b < hp.n_inst; ++b) {
-        const int64_t lo = hp.off[b], hi = hp.off[b + 1], m = hi - lo;
-        double s1, s2, rowmax;
-        host_stats(hp, lo, hi, s1, s2, rowmax);
-        int meth = method;
-        if (meth == 0) meth = m < 10000 ? 1 : 2;
-        double lam;
-        if (meth == 1) {
-            lam = power_lambda_neg(hp, lo, hi, rowmax);
-        } else {
-            const double cnt = static_cast<double>(m) * (m - 1.0);
-            const double mean = cnt > 0 ? s1 / cnt : 0.0;
-            const double var = cnt > 0 ? std::max(0.0, s2 / cnt - mean * mean) : 0.0;
-            lam = 2.0 * std::sqrt(var) * std::sqrt(static_cast<double>(m));
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "output pointers are NULL");
+        if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
+        if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+        HostProblem hp;
+        DOCH_CHECK(load_problem(p, true, hp));
+        for (int b = 0; b < hp.n_inst; ++b) {
+            const int64_t lo = hp.off[b], hi = hp.off[b + 1], m = hi - lo;
+            double s1, s2, rowmax;
+            host_stats(hp, lo, hi, s1, s2, rowmax);
+            int meth = method;
+            if (meth == 0) meth = m < 10000 ? 1 : 2;
+            double lam;
+            if (meth == 1) {
+                lam = power_lambda_neg(hp, lo, hi, rowmax);
+            } else {
+                const double cnt = static_cast<double>(m) * (m - 1.0);
+                const double mean = cnt > 0 ? s1 / cnt : 0.0;
+                const double var = cnt > 0 ? std::max(0.0, s2 / cnt - mean * mean) : 0.0;
+                lam = 2.0 * std::sqrt(var) * std::sqrt(static_cast<double>(m));
+            }
+            const double alpha = eta * lam;
+            alpha_out[b] = alpha;
+            beta_out[b] = std::pow(static_cast<double>(m), 1.5) * (alpha + rowmax);
         }
-        const double alpha = eta * lam;
-        alpha_out[b] = alpha;
-        beta_out[b] = std::pow(static_cast<double>(m), 1.5) * (alpha + rowmax);
-    }
-    return ISING_OK;
+        return ISING_OK;
+    });
 }
 
 ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out) {
-    g_err.clear();
-    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    HostProblem hp;
-    DOCH_CHECK(load_problem(p, !(flags & ISING_FLAG_SKIP_VALIDATION), hp));
-    ising_context *c = new ising_context();
-    ising_status_t s = build_context(hp, flags, c);
-    if (s != ISING_OK) {
-        destroy_ctx(c);
-        return s;
-    }
-    *out = c;
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        HostProblem hp;
+        DOCH_CHECK(load_problem(p, !(flags & ISING_FLAG_SKIP_VALIDATION), hp));
+        ising_context *c = new ising_context();
+        ising_status_t s = build_context(hp, flags, c);
+        if (s != ISING_OK) {
+            destroy_ctx(c);
+            return s;
+        }
+        *out = c;
+        return ISING_OK;
+    });
 }
 
 ising_status_t ising_create_s5(int64_t n, double p, uint64_t seed, int32_t flags, ising_handle_t *out) {
-    g_err.clear();
-    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (n < 2 || n >= (int64_t(1) << 31)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^31 - 1");
-    if (!(p > 0.0) || p > 100.0) return fail(ISING_ERR_INVALID_ARG, "p (percent) must be in (0, 100]");
-    // N_p = floor(102300 / p); keep u < T = ceil(1022 * 2^64 / N_p) (exact in 128-bit integers)
-    const uint64_t np = static_cast<uint64_t>(std::floor(102300.0 / p));
-    const unsigned __int128 num = static_cast<unsigned __int128>(1022) << 64;
-    const uint64_t thr = static_cast<uint64_t>((num + np - 1) / np);
-    ising_context *c = new ising_context();
-    auto bail = [&](ising_status_t s) {
-        destroy_ctx(c);
-        return s;
-    };
-    ising_status_t s;
-    if ((s = [&]() -> ising_status_t {
-             DOCH_CUDA(cudaGetDevice(&c->device));
-             DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-             c->flags = flags;
-             c->format = ISING_FMT_CSR;
-             c->jtype = ISING_I32;
-             c->n = n;
-             c->n_inst = 1;
-             c->inst_off_h = {0, n};
-             c->max_inst_n = n;
-             c->has_h = false;
-             c->integer = true;
-             DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
-             constexpr uint64_t kTagS5 = 13;  // sub-stream tag of the S5 draws
-             DOCH_CHECK(s5_generate(c, n, s5_stream_seed(seed, kTagS5), thr, np));
-             void *ew = nullptr;
-             DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
-             c->err_word = static_cast<int *>(ew);
-             DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
-             void *eh = nullptr;
-             DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
-             c->err_host = static_cast<int *>(eh);
-             *c->err_host = 0;
-             return ISING_OK;
-         }()) != ISING_OK)
-        return bail(s);
-    *out = c;
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        if (n < 2 || n >= (int64_t(1) << 31)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^31 - 1");
+        if (!(p > 0.0) || p > 100.0) return fail(ISING_ERR_INVALID_ARG, "p (percent) must be in (0, 100]");
+        // N_p = floor(102300 / p); keep u < T = ceil(1022 * 2^64 / N_p) (exact in 128-bit integers)
+        const uint64_t np = static_cast<uint64_t>(std::floor(102300.0 / p));
+        const unsigned __int128 num = static_cast<unsigned __int128>(1022) << 64;
+        const uint64_t thr = static_cast<uint64_t>((num + np - 1) / np);
+        ising_context *c = new ising_context();
+        auto bail = [&](ising_status_t s) {
+            destroy_ctx(c);
+            return s;
+        };
+        ising_status_t s;
+        if ((s = [&]() -> ising_status_t {
+                 DOCH_CUDA(cudaGetDevice(&c->device));
+                 DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+                 c->flags = flags;
+                 c->format = ISING_FMT_CSR;
+                 c->jtype = ISING_I32;
+                 c->n = n;
+                 c->n_inst = 1;
+                 c->inst_off_h = {0, n};
+                 c->max_inst_n = n;
+                 c->has_h = false;
+                 c->integer = true;
+                 DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
+                 constexpr uint64_t kTagS5 = 13;  // sub-stream tag of the S5 draws
+                 DOCH_CHECK(s5_generate(c, n, s5_stream_seed(seed, kTagS5), thr, np));
+                 void *ew = nullptr;
+                 DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
+                 c->err_word = static_cast<int *>(ew);
+                 DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
+                 void *eh = nullptr;
+                 DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
+                 c->err_host = static_cast<int *>(eh);
+                 *c->err_host = 0;
+                 return ISING_OK;
+             }()) != ISING_OK)
+            return bail(s);
+        *out = c;
+        return ISING_OK;
+    });
 }
 
 ising_status_t ising_create_procedural(int64_t n, int64_t cst, int32_t flags, ising_handle_t *out) {
-    g_err.clear();
-    if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (n < 2 || n > (int64_t(1) << 30)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^30");
-    if (cst < 0 || cst > (int64_t(1) << 40)) return fail(ISING_ERR_INVALID_ARG, "c must be in 0 .. 2^40");
-    ising_context *c = new ising_context();
-    ising_status_t s = [&]() -> ising_status_t {
-        DOCH_CUDA(cudaGetDevice(&c->device));
-        DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-        c->flags = flags;
-        c->format = ISING_FMT_PROCEDURAL;
-        c->jtype = ISING_F32;
-        c->n = n;
-        c->n_inst = 1;
-        c->inst_off_h = {0, n};
-        c->max_inst_n = n;
-        c->has_h = false;
-        c->integer = false;
-        c->proc_offset = cst;
-        proc_closed_sums(n, cst, &c->proc_s1, &c->proc_s2);
-        DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
-        void *ew = nullptr;
-        DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
-        c->err_word = static_cast<int *>(ew);
-        DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
-        void *eh = nullptr;
-        DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
-        c->err_host = static_cast<int *>(eh);
-        *c->err_host = 0;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!out) return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        if (n < 2 || n > (int64_t(1) << 30)) return fail(ISING_ERR_INVALID_ARG, "n must be in 2 .. 2^30");
+        if (cst < 0 || cst > (int64_t(1) << 40)) return fail(ISING_ERR_INVALID_ARG, "c must be in 0 .. 2^40");
+        ising_context *c = new ising_context();
+        ising_status_t s = [&]() -> ising_status_t {
+            DOCH_CUDA(cudaGetDevice(&c->device));
+            DOCH_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+            c->flags = flags;
+            c->format = ISING_FMT_PROCEDURAL;
+            c->jtype = ISING_F32;
+            c->n = n;
+            c->n_inst = 1;
+            c->inst_off_h = {0, n};
+            c->max_inst_n = n;
+            c->has_h = false;
+            c->integer = false;
+            c->proc_offset = cst;
+            proc_closed_sums(n, cst, &c->proc_s1, &c->proc_s2);
+            DOCH_CHECK(upload(&c->inst_off, c->inst_off_h.data(), sizeof(int64_t) * 2));
+            void *ew = nullptr;
+            DOCH_CUDA(cudaMalloc(&ew, sizeof(int)));
+            c->err_word = static_cast<int *>(ew);
+            DOCH_CUDA(cudaMemset(c->err_word, 0, sizeof(int)));
+            void *eh = nullptr;
+            DOCH_CUDA(cudaMallocHost(&eh, sizeof(int)));
+            c->err_host = static_cast<int *>(eh);
+            *c->err_host = 0;
+            return ISING_OK;
+        }();
+        if (s != ISING_OK) {
+            destroy_ctx(c);
+            return s;
+        }
+        *out = c;
         return ISING_OK;
-    }();
-    if (s != ISING_OK) {
-        destroy_ctx(c);
-        return s;
-    }
-    *out = c;
-    return ISING_OK;
+    });
 }
 
 ising_status_t ising_params_device(ising_handle_t h, double eta, int32_t method, double *alpha_out,
                                    double *beta_out) {
-    g_err.clear();
-    if (!h || !alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
-    if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
-    if (h->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "device parameters run on one instance");
-    if (h->format == ISING_FMT_PROCEDURAL) {
-        if (method == 1) return fail(ISING_ERR_UNSUPPORTED, "PROCEDURAL couplings take the Wigner estimate");
-        return proc_params(h, eta, alpha_out, beta_out);
-    }
-    return params_device(h, eta, method, alpha_out, beta_out);
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !alpha_out || !beta_out) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ISING_ERR_INVALID_ARG, "eta must be > 0");
+        if (method < 0 || method > 2) return fail(ISING_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+        if (h->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "device parameters run on one instance");
+        if (h->format == ISING_FMT_PROCEDURAL) {
+            if (method == 1) return fail(ISING_ERR_UNSUPPORTED, "PROCEDURAL couplings take the Wigner estimate");
+            return proc_params(h, eta, alpha_out, beta_out);
+        }
+        return params_device(h, eta, method, alpha_out, beta_out);
+    });
 }
 
 ising_status_t ising_csr_export(ising_handle_t h, int64_t *row_ptr, int32_t *col, void *val, int64_t *nnz_out,
                                 int32_t *jtype_out) {
-    g_err.clear();
-    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
-    if (h->format != ISING_FMT_CSR) return fail(ISING_ERR_UNSUPPORTED, "the handle does not hold CSR couplings");
-    if (nnz_out) *nnz_out = h->nnz;
-    if (jtype_out) *jtype_out = h->jtype;
-    if (row_ptr) DOCH_CUDA(cudaMemcpy(row_ptr, h->row_ptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDefault));
-    if (col && h->nnz) DOCH_CUDA(cudaMemcpy(col, h->col, sizeof(int32_t) * h->nnz, cudaMemcpyDefault));
-    if (val && h->nnz) DOCH_CUDA(cudaMemcpy(val, h->val, dtype_size(h->jtype) * h->nnz, cudaMemcpyDefault));
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+        if (h->format != ISING_FMT_CSR) return fail(ISING_ERR_UNSUPPORTED, "the handle does not hold CSR couplings");
+        if (nnz_out) *nnz_out = h->nnz;
+        if (jtype_out) *jtype_out = h->jtype;
+        if (row_ptr) DOCH_CUDA(cudaMemcpy(row_ptr, h->row_ptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDefault));
+        if (col && h->nnz) DOCH_CUDA(cudaMemcpy(col, h->col, sizeof(int32_t) * h->nnz, cudaMemcpyDefault));
+        if (val && h->nnz) DOCH_CUDA(cudaMemcpy(val, h->val, dtype_size(h->jtype) * h->nnz, cudaMemcpyDefault));
+        return ISING_OK;
+    });
 }
 
 void ising_destroy(ising_handle_t h) { destroy_ctx(h); }
 
 ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances) {
-    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
-    if (n) *n = h->n;
-    if (n_instances) *n_instances = h->n_inst;
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+        if (n) *n = h->n;
+        if (n_instances) *n_instances = h->n_inst;
+        return ISING_OK;
+    });
 }
 
 ising_status_t ising_synchronize(ising_handle_t h, void *stream) {
-    if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
-    return finish(h, static_cast<cudaStream_t>(stream), true);
+    return doch::guarded([&]() -> ising_status_t {
+        if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+        return finish(h, static_cast<cudaStream_t>(stream), true);
+    });
 }
 
 ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
                              int32_t alpha_len, const double *beta, int32_t iters, double *H_trace,
                              void *stream) {
-    g_err.clear();
-    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    if (R < 1 || iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be >= 1 and iters >= 0");
-    if (alpha_len != 1 && alpha_len != iters) return fail(ISING_ERR_INVALID_ARG, "alpha_len must be 1 or iters");
-    if (h->format == ISING_FMT_DENSE) {
-        if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
-    } else if (h->format == ISING_FMT_PROCEDURAL) {
-        if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
-    } else if (xtype != ISING_F32 && xtype != ISING_F64) {
-        return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
-    }
-    if (R > 65535) return fail(ISING_ERR_INVALID_ARG, "R must be <= 65535");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ising_context *c = h;
-    const int64_t count = c->n * R;
-    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
-    std::vector<double> alpha_h(static_cast<size_t>(c->n_inst) * alpha_len), beta_h(c->n_inst);
-    {
-        std::vector<unsigned char> tmp;
-        DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
-        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
-        DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
-        std::memcpy(beta_h.data(), tmp.data(), tmp.size());
-    }
-    ParamTabs p;
-    DOCH_CHECK(upload_params(c, alpha, alpha_len, beta, p, st));
-
-    const bool x_dev = is_device_ptr(x);
-    void *xd = x;
-    if (!x_dev) {
-        DOCH_CHECK(c->stage_x.ensure(xbytes));
-        xd = c->stage_x.ptr;
-        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
-    }
-    const int pairs = c->n_inst * R;
-    double *Hd = nullptr;
-    if (H_trace) {
-        DOCH_CHECK(c->work.ensure(sizeof(double) * pairs * (static_cast<size_t>(iters) + 1)));
-        Hd = c->work.as<double>();
-    }
-    bool done = false;
-    if (c->format == ISING_FMT_DENSE) {
-        if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for DENSE couplings");
-        if (c->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "DENSE runs one instance");
-        if (iters > 0) DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
-        done = true;
-    }
-    if (!done && !H_trace && c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && iters > 0) {
-        DOCH_CHECK(batched_iterate(c, static_cast<float *>(xd), R, p, iters, st));
-        done = true;
-    }
-    if (!done && !H_trace && c->format == ISING_FMT_CSR && iters > 0) {
-        ising_status_t s = csr_fused(c, xd, xtype, R, p, iters, st);
-        if (s == ISING_OK) done = true;
-        else if (s != ISING_ERR_UNSUPPORTED) return s;
-    }
-    if (!done && iters > 0) {
-        DOCH_CHECK(c->ping.ensure(xbytes));
-        void *cur = xd, *nxt = c->ping.ptr;
-        const bool pairs_ok = !Hd && c->format == ISING_FMT_TORUS2D && xtype == ISING_F32 &&
-                              !(c->flags & ISING_FLAG_SINGLE_STEP) &&
-                              torus_pair_ok(c, static_cast<const float *>(cur), static_cast<const float *>(nxt), R);
-        for (int k = 0; k < iters;) {
-            if (pairs_ok && k + 1 < iters) {  // two steps in one pass over the lattice
-                const double a1 = alpha_h[alpha_len == 1 ? 0 : k], a2 = alpha_h[alpha_len == 1 ? 0 : k + 1];
-                DOCH_CHECK(torus_pair_f32(c, static_cast<const float *>(cur), static_cast<float *>(nxt),
-                                          static_cast<float>(a1), static_cast<float>(a2), 1.0 / beta_h[0], st));
-                std::swap(cur, nxt);
-                k += 2;
-                continue;
-            }
-            if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
-            DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
-            std::swap(cur, nxt);
-            ++k;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        if (R < 1 || iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be >= 1 and iters >= 0");
+        if (alpha_len != 1 && alpha_len != iters) return fail(ISING_ERR_INVALID_ARG, "alpha_len must be 1 or iters");
+        if (h->format == ISING_FMT_DENSE) {
+            if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
+        } else if (h->format == ISING_FMT_PROCEDURAL) {
+            if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+        } else if (xtype != ISING_F32 && xtype != ISING_F64) {
+            return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
         }
-        if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, iters - 1, Hd + static_cast<size_t>(iters) * pairs, st));
-        if (cur != xd) DOCH_CUDA(cudaMemcpyAsync(xd, cur, xbytes, cudaMemcpyDeviceToDevice, st));
-    } else if (!done && Hd) {
-        DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, Hd, st));
-    }
-    bool must_sync = !x_dev;
-    if (!x_dev) DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
-    if (Hd) {
-        const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
-        DOCH_CUDA(cudaMemcpyAsync(H_trace, Hd, hb, cudaMemcpyDefault, st));
-        if (!is_device_ptr(H_trace)) must_sync = true;
-        if (c->flags & ISING_FLAG_STRICT_MONOTONE) {
-            DOCH_CHECK(finish(c, st, true));
-            std::vector<double> Hh(pairs * (static_cast<size_t>(iters) + 1));
-            DOCH_CUDA(cudaMemcpy(Hh.data(), Hd, hb, cudaMemcpyDeviceToHost));
-            for (int k = 0; k < iters; ++k)
-                for (int t = 0; t < pairs; ++t) {
-                    const double a = Hh[static_cast<size_t>(k) * pairs + t], b = Hh[static_cast<size_t>(k + 1) * pairs + t];
-                    if (b > a + 1e-6 * std::fabs(a))
-                        return fail(ISING_ERR_NOT_MONOTONE, "H rose at step " + std::to_string(k));
+        if (R > 65535) return fail(ISING_ERR_INVALID_ARG, "R must be <= 65535");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        ising_context *c = h;
+        const int64_t count = c->n * R;
+        const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+        std::vector<double> alpha_h(static_cast<size_t>(c->n_inst) * alpha_len), beta_h(c->n_inst);
+        {
+            std::vector<unsigned char> tmp;
+            DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
+            std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
+            DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
+            std::memcpy(beta_h.data(), tmp.data(), tmp.size());
+        }
+        ParamTabs p;
+        DOCH_CHECK(upload_params(c, alpha, alpha_len, beta, p, st));
+    
+        const bool x_dev = is_device_ptr(x);
+        void *xd = x;
+        if (!x_dev) {
+            DOCH_CHECK(c->stage_x.ensure(xbytes));
+            xd = c->stage_x.ptr;
+            DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
+        }
+        const int pairs = c->n_inst * R;
+        double *Hd = nullptr;
+        if (H_trace) {
+            DOCH_CHECK(c->work.ensure(sizeof(double) * pairs * (static_cast<size_t>(iters) + 1)));
+            Hd = c->work.as<double>();
+        }
+        bool done = false;
+        if (c->format == ISING_FMT_DENSE) {
+            if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for DENSE couplings");
+            if (c->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "DENSE runs one instance");
+            if (iters > 0) DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
+            done = true;
+        }
+        if (!done && !H_trace && c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && iters > 0) {
+            DOCH_CHECK(batched_iterate(c, static_cast<float *>(xd), R, p, iters, st));
+            done = true;
+        }
+        if (!done && !H_trace && c->format == ISING_FMT_CSR && iters > 0) {
+            ising_status_t s = csr_fused(c, xd, xtype, R, p, iters, st);
+            if (s == ISING_OK) done = true;
+            else if (s != ISING_ERR_UNSUPPORTED) return s;
+        }
+        if (!done && iters > 0) {
+            DOCH_CHECK(c->ping.ensure(xbytes));
+            void *cur = xd, *nxt = c->ping.ptr;
+            const bool pairs_ok = !Hd && c->format == ISING_FMT_TORUS2D && xtype == ISING_F32 &&
+                                  !(c->flags & ISING_FLAG_SINGLE_STEP) &&
+                                  torus_pair_ok(c, static_cast<const float *>(cur), static_cast<const float *>(nxt), R);
+            for (int k = 0; k < iters;) {
+                if (pairs_ok && k + 1 < iters) {  // two steps in one pass over the lattice
+                    const double a1 = alpha_h[alpha_len == 1 ? 0 : k], a2 = alpha_h[alpha_len == 1 ? 0 : k + 1];
+                    DOCH_CHECK(torus_pair_f32(c, static_cast<const float *>(cur), static_cast<float *>(nxt),
+                                              static_cast<float>(a1), static_cast<float>(a2), 1.0 / beta_h[0], st));
+                    std::swap(cur, nxt);
+                    k += 2;
+                    continue;
                 }
+                if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
+                DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+                std::swap(cur, nxt);
+                ++k;
+            }
+            if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, iters - 1, Hd + static_cast<size_t>(iters) * pairs, st));
+            if (cur != xd) DOCH_CUDA(cudaMemcpyAsync(xd, cur, xbytes, cudaMemcpyDeviceToDevice, st));
+        } else if (!done && Hd) {
+            DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, Hd, st));
         }
-    }
-    return finish(c, st, must_sync);
+        bool must_sync = !x_dev;
+        if (!x_dev) DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+        if (Hd) {
+            const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
+            DOCH_CUDA(cudaMemcpyAsync(H_trace, Hd, hb, cudaMemcpyDefault, st));
+            if (!is_device_ptr(H_trace)) must_sync = true;
+            if (c->flags & ISING_FLAG_STRICT_MONOTONE) {
+                DOCH_CHECK(finish(c, st, true));
+                std::vector<double> Hh(pairs * (static_cast<size_t>(iters) + 1));
+                DOCH_CUDA(cudaMemcpy(Hh.data(), Hd, hb, cudaMemcpyDeviceToHost));
+                for (int k = 0; k < iters; ++k)
+                    for (int t = 0; t < pairs; ++t) {
+                        const double a = Hh[static_cast<size_t>(k) * pairs + t], b = Hh[static_cast<size_t>(k + 1) * pairs + t];
+                        if (b > a + 1e-6 * std::fabs(a))
+                            return fail(ISING_ERR_NOT_MONOTONE, "H rose at step " + std::to_string(k));
+                    }
+            }
+        }
+        return finish(c, st, must_sync);
+    });
 }
 
 ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
                                    const double *beta, int32_t iters, int32_t q, int8_t *accepted,
                                    double *H_trace, void *stream) {
-    g_err.clear();
-    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    if (R < 1 || R > 65535 || iters < 0 || q < 0)
-        return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, iters >= 0 and q >= 0");
-    if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
-    ising_context *c = h;
-    if (c->format != ISING_FMT_CSR && c->format != ISING_FMT_TORUS2D && c->format != ISING_FMT_PROCEDURAL)
-        return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR, TORUS2D or PROCEDURAL couplings");
-    if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
-        return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t count = c->n * R;
-    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
-    ParamTabs p;
-    DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
-    const bool x_dev = is_device_ptr(x);
-    void *xd = x;
-    if (!x_dev) {
-        DOCH_CHECK(c->stage_x.ensure(xbytes));
-        xd = c->stage_x.ptr;
-        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
-    }
-    const int pairs = c->n_inst * R;
-    const size_t ab = static_cast<size_t>(pairs) * iters;
-    const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
-    int8_t *acc_dev = nullptr;
-    double *H_dev = nullptr;
-    const bool acc_on_dev = accepted && is_device_ptr(accepted);
-    const bool H_on_dev = H_trace && is_device_ptr(H_trace);
-    if (accepted) {
-        if (acc_on_dev) {
-            acc_dev = accepted;
-        } else {
-            DOCH_CHECK(c->stage_out.ensure(ab + 1));
-            acc_dev = c->stage_out.as<int8_t>();
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        if (R < 1 || R > 65535 || iters < 0 || q < 0)
+            return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, iters >= 0 and q >= 0");
+        if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
+        ising_context *c = h;
+        if (c->format != ISING_FMT_CSR && c->format != ISING_FMT_TORUS2D && c->format != ISING_FMT_PROCEDURAL)
+            return fail(ISING_ERR_UNSUPPORTED, "ADOCH runs on CSR, TORUS2D or PROCEDURAL couplings");
+        if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
+            return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const int64_t count = c->n * R;
+        const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+        ParamTabs p;
+        DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
+        const bool x_dev = is_device_ptr(x);
+        void *xd = x;
+        if (!x_dev) {
+            DOCH_CHECK(c->stage_x.ensure(xbytes));
+            xd = c->stage_x.ptr;
+            DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
         }
-    }
-    if (H_trace) {
-        if (H_on_dev) {
-            H_dev = H_trace;
-        } else {
-            DOCH_CHECK(c->work.ensure(hb));
-            H_dev = c->work.as<double>();
+        const int pairs = c->n_inst * R;
+        const size_t ab = static_cast<size_t>(pairs) * iters;
+        const size_t hb = sizeof(double) * pairs * (static_cast<size_t>(iters) + 1);
+        int8_t *acc_dev = nullptr;
+        double *H_dev = nullptr;
+        const bool acc_on_dev = accepted && is_device_ptr(accepted);
+        const bool H_on_dev = H_trace && is_device_ptr(H_trace);
+        if (accepted) {
+            if (acc_on_dev) {
+                acc_dev = accepted;
+            } else {
+                DOCH_CHECK(c->stage_out.ensure(ab + 1));
+                acc_dev = c->stage_out.as<int8_t>();
+            }
         }
-    }
-    if (iters > 0) DOCH_CHECK(adoch_iterate(c, xd, xtype, R, p, iters, q, acc_dev, H_dev, st));
-    if (H_dev) DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, H_dev + static_cast<size_t>(iters) * pairs, st));
-    bool must_sync = false;
-    if (!x_dev) {
-        DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
-        must_sync = true;
-    }
-    if (accepted && !acc_on_dev && ab > 0) {
-        DOCH_CUDA(cudaMemcpyAsync(accepted, acc_dev, ab, cudaMemcpyDeviceToHost, st));
-        must_sync = true;
-    }
-    if (H_trace && !H_on_dev) {
-        DOCH_CUDA(cudaMemcpyAsync(H_trace, H_dev, hb, cudaMemcpyDeviceToHost, st));
-        must_sync = true;
-    }
-    return finish(c, st, must_sync);
+        if (H_trace) {
+            if (H_on_dev) {
+                H_dev = H_trace;
+            } else {
+                DOCH_CHECK(c->work.ensure(hb));
+                H_dev = c->work.as<double>();
+            }
+        }
+        if (iters > 0) DOCH_CHECK(adoch_iterate(c, xd, xtype, R, p, iters, q, acc_dev, H_dev, st));
+        if (H_dev) DOCH_CHECK(hamiltonian_reduce(c, xd, xtype, R, p, 0, H_dev + static_cast<size_t>(iters) * pairs, st));
+        bool must_sync = false;
+        if (!x_dev) {
+            DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+            must_sync = true;
+        }
+        if (accepted && !acc_on_dev && ab > 0) {
+            DOCH_CUDA(cudaMemcpyAsync(accepted, acc_dev, ab, cudaMemcpyDeviceToHost, st));
+            must_sync = true;
+        }
+        if (H_trace && !H_on_dev) {
+            DOCH_CUDA(cudaMemcpyAsync(H_trace, H_dev, hb, cudaMemcpyDeviceToHost, st));
+            must_sync = true;
+        }
+        return finish(c, st, must_sync);
+    });
 }
 
 ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int32_t R, const double *alpha,
                                    const double *beta, int32_t max_iters, double eps, int32_t *steps_out,
                                    void *stream) {
-    g_err.clear();
-    if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    if (R < 1 || R > 65535 || max_iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, max_iters >= 0");
-    if (!std::isfinite(eps) || eps < 0.0) return fail(ISING_ERR_INVALID_ARG, "eps must be finite and >= 0");
-    if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
-    ising_context *c = h;
-    if (c->format == ISING_FMT_DENSE)
-        return fail(ISING_ERR_UNSUPPORTED, "the stopping rule runs on CSR, TORUS2D or PROCEDURAL");
-    if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
-        return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t count = c->n * R;
-    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
-    const int pairs = c->n_inst * R;
-    std::vector<double> alpha_h(c->n_inst), beta_h(c->n_inst);
-    {
-        std::vector<unsigned char> tmp;
-        DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
-        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
-        DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
-        std::memcpy(beta_h.data(), tmp.data(), tmp.size());
-    }
-    ParamTabs p;
-    DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
-    const bool x_dev = is_device_ptr(x);
-    void *xd = x;
-    if (!x_dev) {
-        DOCH_CHECK(c->stage_x.ensure(xbytes));
-        xd = c->stage_x.ptr;
-        DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
-    }
-    // work: result | partials | running | steps | stopped_now | n_running (256-byte aligned)
-    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
-    const size_t o1 = al(xbytes), o2 = o1 + al(stop_partials_bytes(c, R)), o3 = o2 + al(sizeof(int) * pairs),
-                 o4 = o3 + al(sizeof(int32_t) * pairs), o5 = o4 + al(sizeof(int) * pairs), tot = o5 + 256;
-    DOCH_CHECK(c->work.ensure(tot));
-    unsigned char *wb = c->work.as<unsigned char>();
-    void *res = wb;
-    StopState s;
-    s.partials = reinterpret_cast<double *>(wb + o1);
-    s.running = reinterpret_cast<int *>(wb + o2);
-    s.steps = reinterpret_cast<int32_t *>(wb + o3);
-    s.stopped_now = reinterpret_cast<int *>(wb + o4);
-    s.n_running = reinterpret_cast<int *>(wb + o5);
-    {
-        std::vector<int> ones(pairs, 1), st0(pairs, max_iters);
-        DOCH_CUDA(cudaMemcpyAsync(s.running, ones.data(), sizeof(int) * pairs, cudaMemcpyHostToDevice, st));
-        DOCH_CUDA(cudaMemcpyAsync(s.steps, st0.data(), sizeof(int32_t) * pairs, cudaMemcpyHostToDevice, st));
-        DOCH_CUDA(cudaMemcpyAsync(s.n_running, &pairs, sizeof(int), cudaMemcpyHostToDevice, st));
-        DOCH_CUDA(cudaMemsetAsync(s.stopped_now, 0, sizeof(int) * pairs, st));
-        DOCH_CUDA(cudaStreamSynchronize(st));  // the sources are pageable
-    }
-    // batched FP32 instances: the rule runs inside the shared-memory resident kernel, which
-    // ends each (instance, replica group) as soon as all of its replicas stopped
-    ising_status_t rs = ISING_ERR_UNSUPPORTED;
-    if (c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && max_iters > 0)
-        rs = batched_resident_launch(c, static_cast<float *>(xd), R, p, max_iters, st, static_cast<float>(eps),
-                                     s.steps);
-    if (rs != ISING_OK && rs != ISING_ERR_UNSUPPORTED) return rs;
-    if (rs == ISING_ERR_UNSUPPORTED) {
-        if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
-        DOCH_CHECK(c->ping.ensure(xbytes));
-        void *cur = xd, *nxt = c->ping.ptr;
-        constexpr int kPoll = 8;  // steps between host checks of the running-pair count
-        for (int k = 0; k < max_iters; ++k) {
-            DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
-            DOCH_CHECK(stop_step(c, cur, nxt, res, xtype, R, eps, k, s, st));
-            std::swap(cur, nxt);
-            if ((k + 1) % kPoll == 0 && k + 1 < max_iters) {
-                DOCH_CUDA(cudaMemcpyAsync(c->count_host, s.n_running, sizeof(int), cudaMemcpyDeviceToHost, st));
-                DOCH_CUDA(cudaStreamSynchronize(st));
-                if (*c->count_host == 0) break;
-            }
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x || !alpha || !beta) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        if (R < 1 || R > 65535 || max_iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be in 1..65535, max_iters >= 0");
+        if (!std::isfinite(eps) || eps < 0.0) return fail(ISING_ERR_INVALID_ARG, "eps must be finite and >= 0");
+        if (xtype != ISING_F32 && xtype != ISING_F64) return fail(ISING_ERR_INVALID_ARG, "iterates must be F32 or F64");
+        ising_context *c = h;
+        if (c->format == ISING_FMT_DENSE)
+            return fail(ISING_ERR_UNSUPPORTED, "the stopping rule runs on CSR, TORUS2D or PROCEDURAL");
+        if (c->format == ISING_FMT_PROCEDURAL && xtype != ISING_F32)
+            return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const int64_t count = c->n * R;
+        const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+        const int pairs = c->n_inst * R;
+        std::vector<double> alpha_h(c->n_inst), beta_h(c->n_inst);
+        {
+            std::vector<unsigned char> tmp;
+            DOCH_CHECK(to_host(alpha, sizeof(double) * alpha_h.size(), tmp));
+            std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
+            DOCH_CHECK(to_host(beta, sizeof(double) * beta_h.size(), tmp));
+            std::memcpy(beta_h.data(), tmp.data(), tmp.size());
         }
-        DOCH_CHECK(stop_finish(c, cur, res, xtype, R, s, st));
-        DOCH_CUDA(cudaMemcpyAsync(xd, res, xbytes, cudaMemcpyDeviceToDevice, st));
-    }
-    bool must_sync = false;
-    if (!x_dev) {
-        DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
-        must_sync = true;
-    }
-    if (steps_out) {
-        DOCH_CUDA(cudaMemcpyAsync(steps_out, s.steps, sizeof(int32_t) * pairs, cudaMemcpyDefault, st));
-        if (!is_device_ptr(steps_out)) must_sync = true;
-    }
-    return finish(c, st, must_sync);
+        ParamTabs p;
+        DOCH_CHECK(upload_params(c, alpha, 1, beta, p, st));
+        const bool x_dev = is_device_ptr(x);
+        void *xd = x;
+        if (!x_dev) {
+            DOCH_CHECK(c->stage_x.ensure(xbytes));
+            xd = c->stage_x.ptr;
+            DOCH_CUDA(cudaMemcpyAsync(xd, x, xbytes, cudaMemcpyHostToDevice, st));
+        }
+        // work: result | partials | running | steps | stopped_now | n_running (256-byte aligned)
+        auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+        const size_t o1 = al(xbytes), o2 = o1 + al(stop_partials_bytes(c, R)), o3 = o2 + al(sizeof(int) * pairs),
+                     o4 = o3 + al(sizeof(int32_t) * pairs), o5 = o4 + al(sizeof(int) * pairs), tot = o5 + 256;
+        DOCH_CHECK(c->work.ensure(tot));
+        unsigned char *wb = c->work.as<unsigned char>();
+        void *res = wb;
+        StopState s;
+        s.partials = reinterpret_cast<double *>(wb + o1);
+        s.running = reinterpret_cast<int *>(wb + o2);
+        s.steps = reinterpret_cast<int32_t *>(wb + o3);
+        s.stopped_now = reinterpret_cast<int *>(wb + o4);
+        s.n_running = reinterpret_cast<int *>(wb + o5);
+        {
+            std::vector<int> ones(pairs, 1), st0(pairs, max_iters);
+            DOCH_CUDA(cudaMemcpyAsync(s.running, ones.data(), sizeof(int) * pairs, cudaMemcpyHostToDevice, st));
+            DOCH_CUDA(cudaMemcpyAsync(s.steps, st0.data(), sizeof(int32_t) * pairs, cudaMemcpyHostToDevice, st));
+            DOCH_CUDA(cudaMemcpyAsync(s.n_running, &pairs, sizeof(int), cudaMemcpyHostToDevice, st));
+            DOCH_CUDA(cudaMemsetAsync(s.stopped_now, 0, sizeof(int) * pairs, st));
+            DOCH_CUDA(cudaStreamSynchronize(st));  // the sources are pageable
+        }
+        // batched FP32 instances: the rule runs inside the shared-memory resident kernel, which
+        // ends each (instance, replica group) as soon as all of its replicas stopped
+        ising_status_t rs = ISING_ERR_UNSUPPORTED;
+        if (c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && max_iters > 0)
+            rs = batched_resident_launch(c, static_cast<float *>(xd), R, p, max_iters, st, static_cast<float>(eps),
+                                         s.steps);
+        if (rs != ISING_OK && rs != ISING_ERR_UNSUPPORTED) return rs;
+        if (rs == ISING_ERR_UNSUPPORTED) {
+            if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
+            DOCH_CHECK(c->ping.ensure(xbytes));
+            void *cur = xd, *nxt = c->ping.ptr;
+            constexpr int kPoll = 8;  // steps between host checks of the running-pair count
+            for (int k = 0; k < max_iters; ++k) {
+                DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+                DOCH_CHECK(stop_step(c, cur, nxt, res, xtype, R, eps, k, s, st));
+                std::swap(cur, nxt);
+                if ((k + 1) % kPoll == 0 && k + 1 < max_iters) {
+                    DOCH_CUDA(cudaMemcpyAsync(c->count_host, s.n_running, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DOCH_CUDA(cudaStreamSynchronize(st));
+                    if (*c->count_host == 0) break;
+                }
+            }
+            DOCH_CHECK(stop_finish(c, cur, res, xtype, R, s, st));
+            DOCH_CUDA(cudaMemcpyAsync(xd, res, xbytes, cudaMemcpyDeviceToDevice, st));
+        }
+        bool must_sync = false;
+        if (!x_dev) {
+            DOCH_CUDA(cudaMemcpyAsync(x, xd, xbytes, cudaMemcpyDeviceToHost, st));
+            must_sync = true;
+        }
+        if (steps_out) {
+            DOCH_CUDA(cudaMemcpyAsync(steps_out, s.steps, sizeof(int32_t) * pairs, cudaMemcpyDefault, st));
+            if (!is_device_ptr(steps_out)) must_sync = true;
+        }
+        return finish(c, st, must_sync);
+    });
 }
 
 ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int32_t R, int64_t *E_int,
                             int64_t *cut_int, double *E_f64, double *cut_f64, int32_t *best, int8_t *spins,
                             void *stream) {
-    g_err.clear();
-    if (!h || !x) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    if (R < 1 || R > 65535) return fail(ISING_ERR_INVALID_ARG, "R out of range");
-    if (xtype != ISING_F32 && xtype != ISING_F64 && xtype != ISING_BF16 && xtype != ISING_I8)
-        return fail(ISING_ERR_INVALID_ARG, "x must be F32, F64, BF16 or I8");
-    ising_context *c = h;
-    if ((E_int || cut_int) && !c->integer)
-        return fail(ISING_ERR_INVALID_ARG, "integer energies need integer couplings and field");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t count = c->n * R;
-    const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
-    const void *xd = x;
-    bool must_sync = false;
-    if (!is_device_ptr(x)) {
-        DOCH_CHECK(c->stage_x.ensure(xbytes));
-        DOCH_CUDA(cudaMemcpyAsync(c->stage_x.ptr, x, xbytes, cudaMemcpyHostToDevice, st));
-        xd = c->stage_x.ptr;
-        must_sync = true;
-    }
-    const size_t pairs = static_cast<size_t>(c->n_inst) * R;
-    // staging of the outputs: E_i | cut_i | E_d | cut_d | best
-    DOCH_CHECK(c->stage_out.ensure(pairs * 8 * 4 + c->n_inst * 4 + 64));
-    int64_t *Ei = c->stage_out.as<int64_t>();
-    int64_t *Ci = Ei + pairs;
-    double *Ed = reinterpret_cast<double *>(Ci + pairs);
-    double *Cd = Ed + pairs;
-    int32_t *Bd = reinterpret_cast<int32_t *>(Cd + pairs);
-    if (c->format == ISING_FMT_DENSE)
-        DOCH_CHECK(dense_energy(c, xd, xtype, R, Ei, Ci, Ed, Cd, st));
-    else if (c->format == ISING_FMT_PROCEDURAL)
-        DOCH_CHECK(proc_energy(c, xd, xtype, R, Ed, Cd, st));
-    else
-        DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
-    if (best) DOCH_CHECK(best_replica(c, c->integer ? Ei : nullptr, Ed, R, Bd, st));
-    auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
-        if (!dst) return ISING_OK;
-        if (!is_device_ptr(dst)) must_sync = true;
-        DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
-        return ISING_OK;
-    };
-    DOCH_CHECK(put(E_int, Ei, pairs * 8));
-    DOCH_CHECK(put(cut_int, Ci, pairs * 8));
-    DOCH_CHECK(put(E_f64, Ed, pairs * 8));
-    DOCH_CHECK(put(cut_f64, Cd, pairs * 8));
-    DOCH_CHECK(put(best, Bd, c->n_inst * 4));
-    if (spins) {
-        if (is_device_ptr(spins)) {
-            DOCH_CHECK(write_spins(c, xd, xtype, R, spins, st));
-        } else {
-            DOCH_CHECK(c->work.ensure(count));
-            DOCH_CHECK(write_spins(c, xd, xtype, R, c->work.as<int8_t>(), st));
-            DOCH_CUDA(cudaMemcpyAsync(spins, c->work.ptr, count, cudaMemcpyDeviceToHost, st));
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        if (R < 1 || R > 65535) return fail(ISING_ERR_INVALID_ARG, "R out of range");
+        if (xtype != ISING_F32 && xtype != ISING_F64 && xtype != ISING_BF16 && xtype != ISING_I8)
+            return fail(ISING_ERR_INVALID_ARG, "x must be F32, F64, BF16 or I8");
+        ising_context *c = h;
+        if ((E_int || cut_int) && !c->integer)
+            return fail(ISING_ERR_INVALID_ARG, "integer energies need integer couplings and field");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const int64_t count = c->n * R;
+        const size_t xbytes = static_cast<size_t>(count) * xtype_size(xtype);
+        const void *xd = x;
+        bool must_sync = false;
+        if (!is_device_ptr(x)) {
+            DOCH_CHECK(c->stage_x.ensure(xbytes));
+            DOCH_CUDA(cudaMemcpyAsync(c->stage_x.ptr, x, xbytes, cudaMemcpyHostToDevice, st));
+            xd = c->stage_x.ptr;
             must_sync = true;
         }
-    }
-    return finish(c, st, must_sync);
+        const size_t pairs = static_cast<size_t>(c->n_inst) * R;
+        // staging of the outputs: E_i | cut_i | E_d | cut_d | best
+        DOCH_CHECK(c->stage_out.ensure(pairs * 8 * 4 + c->n_inst * 4 + 64));
+        int64_t *Ei = c->stage_out.as<int64_t>();
+        int64_t *Ci = Ei + pairs;
+        double *Ed = reinterpret_cast<double *>(Ci + pairs);
+        double *Cd = Ed + pairs;
+        int32_t *Bd = reinterpret_cast<int32_t *>(Cd + pairs);
+        if (c->format == ISING_FMT_DENSE)
+            DOCH_CHECK(dense_energy(c, xd, xtype, R, Ei, Ci, Ed, Cd, st));
+        else if (c->format == ISING_FMT_PROCEDURAL)
+            DOCH_CHECK(proc_energy(c, xd, xtype, R, Ed, Cd, st));
+        else
+            DOCH_CHECK(energy_reduce(c, xd, xtype, R, c->integer ? Ei : nullptr, c->integer ? Ci : nullptr, Ed, Cd, st));
+        if (best) DOCH_CHECK(best_replica(c, c->integer ? Ei : nullptr, Ed, R, Bd, st));
+        auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
+            if (!dst) return ISING_OK;
+            if (!is_device_ptr(dst)) must_sync = true;
+            DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+            return ISING_OK;
+        };
+        DOCH_CHECK(put(E_int, Ei, pairs * 8));
+        DOCH_CHECK(put(cut_int, Ci, pairs * 8));
+        DOCH_CHECK(put(E_f64, Ed, pairs * 8));
+        DOCH_CHECK(put(cut_f64, Cd, pairs * 8));
+        DOCH_CHECK(put(best, Bd, c->n_inst * 4));
+        if (spins) {
+            if (is_device_ptr(spins)) {
+                DOCH_CHECK(write_spins(c, xd, xtype, R, spins, st));
+            } else {
+                DOCH_CHECK(c->work.ensure(count));
+                DOCH_CHECK(write_spins(c, xd, xtype, R, c->work.as<int8_t>(), st));
+                DOCH_CUDA(cudaMemcpyAsync(spins, c->work.ptr, count, cudaMemcpyDeviceToHost, st));
+                must_sync = true;
+            }
+        }
+        return finish(c, st, must_sync);
+    });
 }
 
 ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, int32_t R, const double *alpha,
                               int32_t iters, double beta, int32_t ckpt_every, double *grad_alpha,
                               void *grad_x0, double *loss, int64_t *zero_events, void *stream) {
-    g_err.clear();
-    if (!h || !x0 || !alpha) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
-    ising_context *c = h;
-    if (c->format != ISING_FMT_CSR || c->n_inst != 1)
-        return fail(ISING_ERR_UNSUPPORTED, "ising_backward runs on one CSR instance");
-    if (xtype != ISING_F32 && xtype != ISING_F64)
-        return fail(ISING_ERR_INVALID_ARG, "ising_backward iterates are F32 or F64");
-    const size_t xel = xtype == ISING_F64 ? 8 : 4;
-    if (R < 1 || R > 65535 || iters < 1 || ckpt_every < 1)
-        return fail(ISING_ERR_INVALID_ARG, "need 1 <= R <= 65535, iters >= 1, ckpt_every >= 1");
-    if (!std::isfinite(beta) || beta <= 0.0) return fail(ISING_ERR_INVALID_ARG, "beta must be finite and > 0");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int C = ckpt_every < iters ? ckpt_every : iters;
-    const int S = (iters + C - 1) / C;                   // checkpoints x^(sC), s = 0..S-1
-    std::vector<double> alpha_h(iters);
-    {
-        std::vector<unsigned char> tmp;
-        DOCH_CHECK(to_host(alpha, sizeof(double) * iters, tmp));
-        std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
-    }
-    ParamTabs p;
-    DOCH_CHECK(upload_params(c, alpha_h.data(), iters, &beta, p, st));
-    const int V = (R % 4 == 0) ? 4 : (R % 2 == 0 ? 2 : 1);
-    if (R / V > 256) return fail(ISING_ERR_UNSUPPORTED, "ising_backward: R / vector width must be <= 256");
-    const int64_t rows_per_block = 256 / (R / V);
-    int64_t grid64 = (c->n + rows_per_block - 1) / rows_per_block;
-    if (grid64 > 8LL * c->num_sms) grid64 = 8LL * c->num_sms;
-    const int grid = static_cast<int>(grid64 < 1 ? 1 : grid64);
-    // layout of the handle's checkpoint buffer
-    auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
-    const size_t A = al(static_cast<size_t>(c->n) * R * xel);        // one iterate
-    const size_t G = al(static_cast<size_t>(c->n) * R * sizeof(float)); // one adjoint state
-    const size_t part_b = al(sizeof(double) * static_cast<size_t>(iters) * grid);
-    const size_t lpart_b = al(sizeof(double) * grid);
-    const size_t out_b = al(sizeof(double) * (static_cast<size_t>(iters) + 1) + 8);
-    const size_t wide_b = xtype == ISING_F64 ? A : 0;                   // FP64 copy of dL/dx0
-    DOCH_CHECK(c->ckpt.ensure(A * (S + C) + 2 * G + wide_b + part_b + lpart_b + out_b));
-    unsigned char *base = c->ckpt.as<unsigned char>();
-    auto ck = [&](int sg_i) { return static_cast<void *>(base + A * sg_i); };
-    auto sg = [&](int m) { return static_cast<void *>(base + A * (S + m)); };
-    unsigned char *tail = base + A * (S + C);
-    float *gbuf[2] = {reinterpret_cast<float *>(tail), reinterpret_cast<float *>(tail + G)};
-    double *wide = reinterpret_cast<double *>(tail + 2 * G);
-    double *part = reinterpret_cast<double *>(tail + 2 * G + wide_b);
-    double *lpart = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b);
-    double *ga_d = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b + lpart_b);
-    double *loss_d = ga_d + iters;
-    unsigned long long *zeros_d = reinterpret_cast<unsigned long long *>(loss_d + 1);
-    DOCH_CUDA(cudaMemsetAsync(zeros_d, 0, 8, st));
-    const size_t xbytes = static_cast<size_t>(c->n) * R * xel;
-    DOCH_CUDA(cudaMemcpyAsync(ck(0), x0, xbytes, cudaMemcpyDefault, st));
-    // x^(sC + m) of segment s: checkpoint, recomputed iterate, or the next checkpoint
-    auto seg_len = [&](int sg_i) { return std::min(C, iters - sg_i * C); };
-    auto xs = [&](int sg_i, int m) -> void * {
-        if (m == 0) return ck(sg_i);
-        if (m == seg_len(sg_i) && sg_i + 1 < S) return ck(sg_i + 1);
-        return sg(m - 1);
-    };
-    // forward: all segments, storing the checkpoints
-    for (int sg_i = 0; sg_i < S; ++sg_i)
-        for (int m = 1; m <= seg_len(sg_i); ++m)
-            DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
-    // loss and g^N (x^N is the last iterate of the last segment)
-    int gc = 0;
-    DOCH_CHECK(csr_loss_grad(c, xs(S - 1, seg_len(S - 1)), xtype, gbuf[gc], R, V, grid, lpart, st));
-    const float inv_beta = static_cast<float>(1.0 / beta);
-    for (int sg_i = S - 1; sg_i >= 0; --sg_i) {
-        const int len = seg_len(sg_i);
-        if (sg_i < S - 1)  // the last segment's iterates are still in place from the forward pass
-            for (int m = 1; m < len; ++m)
-                DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
-        for (int m = len - 1; m >= 0; --m) {
-            const int k = sg_i * C + m;
-            DOCH_CHECK(csr_adjoint_step(c, gbuf[gc], xs(sg_i, m + 1), xs(sg_i, m), xtype, gbuf[1 - gc], R, V,
-                                        static_cast<float>(alpha_h[k]), inv_beta, grid,
-                                        part + static_cast<size_t>(k) * grid, zeros_d, st));
-            gc = 1 - gc;
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x0 || !alpha) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        ising_context *c = h;
+        if (c->format != ISING_FMT_CSR || c->n_inst != 1)
+            return fail(ISING_ERR_UNSUPPORTED, "ising_backward runs on one CSR instance");
+        if (xtype != ISING_F32 && xtype != ISING_F64)
+            return fail(ISING_ERR_INVALID_ARG, "ising_backward iterates are F32 or F64");
+        const size_t xel = xtype == ISING_F64 ? 8 : 4;
+        if (R < 1 || R > 65535 || iters < 1 || ckpt_every < 1)
+            return fail(ISING_ERR_INVALID_ARG, "need 1 <= R <= 65535, iters >= 1, ckpt_every >= 1");
+        if (!std::isfinite(beta) || beta <= 0.0) return fail(ISING_ERR_INVALID_ARG, "beta must be finite and > 0");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const int C = ckpt_every < iters ? ckpt_every : iters;
+        const int S = (iters + C - 1) / C;                   // checkpoints x^(sC), s = 0..S-1
+        std::vector<double> alpha_h(iters);
+        {
+            std::vector<unsigned char> tmp;
+            DOCH_CHECK(to_host(alpha, sizeof(double) * iters, tmp));
+            std::memcpy(alpha_h.data(), tmp.data(), tmp.size());
         }
-    }
-    DOCH_CHECK(adjoint_finish_launch(part, iters, grid, beta, lpart, grid, R, ga_d, loss_d, st));
-    bool must_sync = false;
-    auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
-        if (!dst) return ISING_OK;
-        if (!is_device_ptr(dst)) must_sync = true;
-        DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
-        return ISING_OK;
-    };
-    if (xtype == ISING_F64) {
-        DOCH_CHECK(widen_f32_to_f64(gbuf[gc], wide, c->n * R, c->num_sms, st));
-        DOCH_CHECK(put(grad_x0, wide, xbytes));
-    } else {
-        DOCH_CHECK(put(grad_x0, gbuf[gc], xbytes));
-    }
-    DOCH_CHECK(put(grad_alpha, ga_d, sizeof(double) * iters));
-    DOCH_CHECK(put(loss, loss_d, sizeof(double)));
-    DOCH_CHECK(put(zero_events, zeros_d, sizeof(int64_t)));
-    if (!is_device_ptr(x0)) must_sync = true;
-    return finish(c, st, must_sync);
+        ParamTabs p;
+        DOCH_CHECK(upload_params(c, alpha_h.data(), iters, &beta, p, st));
+        const int V = (R % 4 == 0) ? 4 : (R % 2 == 0 ? 2 : 1);
+        if (R / V > 256) return fail(ISING_ERR_UNSUPPORTED, "ising_backward: R / vector width must be <= 256");
+        const int64_t rows_per_block = 256 / (R / V);
+        int64_t grid64 = (c->n + rows_per_block - 1) / rows_per_block;
+        if (grid64 > 8LL * c->num_sms) grid64 = 8LL * c->num_sms;
+        const int grid = static_cast<int>(grid64 < 1 ? 1 : grid64);
+        // layout of the handle's checkpoint buffer
+        auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+        const size_t A = al(static_cast<size_t>(c->n) * R * xel);        // one iterate
+        const size_t G = al(static_cast<size_t>(c->n) * R * sizeof(float)); // one adjoint state
+        const size_t part_b = al(sizeof(double) * static_cast<size_t>(iters) * grid);
+        const size_t lpart_b = al(sizeof(double) * grid);
+        const size_t out_b = al(sizeof(double) * (static_cast<size_t>(iters) + 1) + 8);
+        const size_t wide_b = xtype == ISING_F64 ? A : 0;                   // FP64 copy of dL/dx0
+        DOCH_CHECK(c->ckpt.ensure(A * (S + C) + 2 * G + wide_b + part_b + lpart_b + out_b));
+        unsigned char *base = c->ckpt.as<unsigned char>();
+        auto ck = [&](int sg_i) { return static_cast<void *>(base + A * sg_i); };
+        auto sg = [&](int m) { return static_cast<void *>(base + A * (S + m)); };
+        unsigned char *tail = base + A * (S + C);
+        float *gbuf[2] = {reinterpret_cast<float *>(tail), reinterpret_cast<float *>(tail + G)};
+        double *wide = reinterpret_cast<double *>(tail + 2 * G);
+        double *part = reinterpret_cast<double *>(tail + 2 * G + wide_b);
+        double *lpart = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b);
+        double *ga_d = reinterpret_cast<double *>(tail + 2 * G + wide_b + part_b + lpart_b);
+        double *loss_d = ga_d + iters;
+        unsigned long long *zeros_d = reinterpret_cast<unsigned long long *>(loss_d + 1);
+        DOCH_CUDA(cudaMemsetAsync(zeros_d, 0, 8, st));
+        const size_t xbytes = static_cast<size_t>(c->n) * R * xel;
+        DOCH_CUDA(cudaMemcpyAsync(ck(0), x0, xbytes, cudaMemcpyDefault, st));
+        // x^(sC + m) of segment s: checkpoint, recomputed iterate, or the next checkpoint
+        auto seg_len = [&](int sg_i) { return std::min(C, iters - sg_i * C); };
+        auto xs = [&](int sg_i, int m) -> void * {
+            if (m == 0) return ck(sg_i);
+            if (m == seg_len(sg_i) && sg_i + 1 < S) return ck(sg_i + 1);
+            return sg(m - 1);
+        };
+        // forward: all segments, storing the checkpoints
+        for (int sg_i = 0; sg_i < S; ++sg_i)
+            for (int m = 1; m <= seg_len(sg_i); ++m)
+                DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
+        // loss and g^N (x^N is the last iterate of the last segment)
+        int gc = 0;
+        DOCH_CHECK(csr_loss_grad(c, xs(S - 1, seg_len(S - 1)), xtype, gbuf[gc], R, V, grid, lpart, st));
+        const float inv_beta = static_cast<float>(1.0 / beta);
+        for (int sg_i = S - 1; sg_i >= 0; --sg_i) {
+            const int len = seg_len(sg_i);
+            if (sg_i < S - 1)  // the last segment's iterates are still in place from the forward pass
+                for (int m = 1; m < len; ++m)
+                    DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
+            for (int m = len - 1; m >= 0; --m) {
+                const int k = sg_i * C + m;
+                DOCH_CHECK(csr_adjoint_step(c, gbuf[gc], xs(sg_i, m + 1), xs(sg_i, m), xtype, gbuf[1 - gc], R, V,
+                                            static_cast<float>(alpha_h[k]), inv_beta, grid,
+                                            part + static_cast<size_t>(k) * grid, zeros_d, st));
+                gc = 1 - gc;
+            }
+        }
+        DOCH_CHECK(adjoint_finish_launch(part, iters, grid, beta, lpart, grid, R, ga_d, loss_d, st));
+        bool must_sync = false;
+        auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
+            if (!dst) return ISING_OK;
+            if (!is_device_ptr(dst)) must_sync = true;
+            DOCH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+            return ISING_OK;
+        };
+        if (xtype == ISING_F64) {
+            DOCH_CHECK(widen_f32_to_f64(gbuf[gc], wide, c->n * R, c->num_sms, st));
+            DOCH_CHECK(put(grad_x0, wide, xbytes));
+        } else {
+            DOCH_CHECK(put(grad_x0, gbuf[gc], xbytes));
+        }
+        DOCH_CHECK(put(grad_alpha, ga_d, sizeof(double) * iters));
+        DOCH_CHECK(put(loss, loss_d, sizeof(double)));
+        DOCH_CHECK(put(zero_events, zeros_d, sizeof(int64_t)));
+        if (!is_device_ptr(x0)) must_sync = true;
+        return finish(c, st, must_sync);
+    });
 }
 
 }  // extern "C"

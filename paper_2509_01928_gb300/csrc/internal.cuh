@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -18,6 +20,21 @@ namespace doch {
 void set_error(const std::string &msg);
 ising_status_t fail(ising_status_t s, const std::string &msg);
 ising_status_t cuda_fail(cudaError_t e, const char *what);
+
+// Runs the body of a C-ABI entry point: a host exception (a failed allocation, ...) becomes a
+// status instead of leaving through extern "C".
+template <typename F>
+ising_status_t guarded(F &&f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return fail(ISING_ERR_OOM, "host memory allocation failed");
+    } catch (const std::exception &e) {
+        return fail(ISING_ERR_INVALID_ARG, std::string("host error: ") + e.what());
+    } catch (...) {
+        return fail(ISING_ERR_INVALID_ARG, "host error");
+    }
+}
 
 // (the locals carry a long prefix so that they cannot capture a name used in the argument)
 #define DOCH_CUDA(call)                                                          \

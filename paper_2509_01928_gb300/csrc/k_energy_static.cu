@@ -117,38 +117,40 @@ extern "C" ising_status_t ising_energy_torus_noalloc(const int8_t *right, const 
                                                      int64_t l_rows, int64_t l_cols, const float *x,
                                                      int32_t R, int64_t *E_out, int64_t *cut_out,
                                                      void *stream) {
-    using namespace doch;
-    if (!right || !down || !x || (!E_out && !cut_out))
-        return fail(ISING_ERR_INVALID_ARG, "noalloc energy: NULL argument");
-    if (l_rows < 2 || l_cols < 2) return fail(ISING_ERR_INVALID_ARG, "noalloc energy: l_rows, l_cols must be >= 2");
-    if (R < 1) return fail(ISING_ERR_INVALID_ARG, "noalloc energy: R must be >= 1");
-    if (R > kStaticReplicas)
-        return fail(ISING_ERR_INVALID_ARG, "noalloc energy: R exceeds the static scratch capacity of " +
-                                               std::to_string(kStaticReplicas) + " replicas");
-    if (!on_device(right) || !on_device(down) || !on_device(x) || (E_out && !on_device(E_out)) ||
-        (cut_out && !on_device(cut_out)))
-        return fail(ISING_ERR_INVALID_ARG, "noalloc energy: every array must be device memory");
-    long long *partials = nullptr;
-    DOCH_CHECK(static_partials(&partials));
-    int dev = 0, sms = 1;
-    DOCH_CUDA(cudaGetDevice(&dev));
-    DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t n = l_rows * l_cols;
-    int64_t chunks = (4LL * sms + R - 1) / R;
-    const int64_t cap_slots = kStaticReplicas / R;       // chunks that fit for this R
-    const int64_t cap_sites = (n + kThreadsS - 1) / kThreadsS;
-    if (chunks > cap_slots) chunks = cap_slots;
-    if (chunks > cap_sites) chunks = cap_sites;
-    if (chunks > 65535) chunks = 65535;
-    if (chunks < 1) chunks = 1;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // every partial read by the finisher is written by this call first: no clearing needed
-    dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(R));
-    torus_energy_partials_static<<<grid, kThreadsS, 0, st>>>(right, down, l_rows, l_cols, x, R,
-                                                            static_cast<int>(chunks), partials);
-    DOCH_CUDA(cudaGetLastError());
-    torus_energy_finish_static<<<(R + 127) / 128, 128, 0, st>>>(partials, R, static_cast<int>(chunks),
-                                                               E_out, cut_out);
-    DOCH_CUDA(cudaGetLastError());
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        using namespace doch;
+        if (!right || !down || !x || (!E_out && !cut_out))
+            return fail(ISING_ERR_INVALID_ARG, "noalloc energy: NULL argument");
+        if (l_rows < 2 || l_cols < 2) return fail(ISING_ERR_INVALID_ARG, "noalloc energy: l_rows, l_cols must be >= 2");
+        if (R < 1) return fail(ISING_ERR_INVALID_ARG, "noalloc energy: R must be >= 1");
+        if (R > kStaticReplicas)
+            return fail(ISING_ERR_INVALID_ARG, "noalloc energy: R exceeds the static scratch capacity of " +
+                                                   std::to_string(kStaticReplicas) + " replicas");
+        if (!on_device(right) || !on_device(down) || !on_device(x) || (E_out && !on_device(E_out)) ||
+            (cut_out && !on_device(cut_out)))
+            return fail(ISING_ERR_INVALID_ARG, "noalloc energy: every array must be device memory");
+        long long *partials = nullptr;
+        DOCH_CHECK(static_partials(&partials));
+        int dev = 0, sms = 1;
+        DOCH_CUDA(cudaGetDevice(&dev));
+        DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t n = l_rows * l_cols;
+        int64_t chunks = (4LL * sms + R - 1) / R;
+        const int64_t cap_slots = kStaticReplicas / R;       // chunks that fit for this R
+        const int64_t cap_sites = (n + kThreadsS - 1) / kThreadsS;
+        if (chunks > cap_slots) chunks = cap_slots;
+        if (chunks > cap_sites) chunks = cap_sites;
+        if (chunks > 65535) chunks = 65535;
+        if (chunks < 1) chunks = 1;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        // every partial read by the finisher is written by this call first: no clearing needed
+        dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(R));
+        torus_energy_partials_static<<<grid, kThreadsS, 0, st>>>(right, down, l_rows, l_cols, x, R,
+                                                                static_cast<int>(chunks), partials);
+        DOCH_CUDA(cudaGetLastError());
+        torus_energy_finish_static<<<(R + 127) / 128, 128, 0, st>>>(partials, R, static_cast<int>(chunks),
+                                                                   E_out, cut_out);
+        DOCH_CUDA(cudaGetLastError());
+        return ISING_OK;
+    });
 }

@@ -751,14 +751,16 @@ ising_status_t proc_params(ising_context *c, double eta, double *alpha, double *
 
 extern "C" ising_status_t ising_selftest_procedural(int64_t row0, int32_t rows, int64_t col0, int32_t cols,
                                                     int64_t c, float *J_out, void *stream) {
-    using namespace doch;
-    if (!J_out || row0 < 0 || col0 < 0 || rows < 0 || cols < 0 || c < 0 || c > (int64_t(1) << 40) ||
-        row0 + rows > (int64_t(1) << 30) || col0 + cols > (int64_t(1) << 30))
-        return fail(ISING_ERR_INVALID_ARG, "selftest_procedural: bad argument");
-    if (rows == 0 || cols == 0) return ISING_OK;
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    proc_couplings<<<(rows + 127) / 128, 128, 0, st>>>(row0, rows, col0, cols, c, J_out);
-    DOCH_CUDA(cudaGetLastError());
-    DOCH_CUDA(cudaStreamSynchronize(st));
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        using namespace doch;
+        if (!J_out || row0 < 0 || col0 < 0 || rows < 0 || cols < 0 || c < 0 || c > (int64_t(1) << 40) ||
+            row0 + rows > (int64_t(1) << 30) || col0 + cols > (int64_t(1) << 30))
+            return fail(ISING_ERR_INVALID_ARG, "selftest_procedural: bad argument");
+        if (rows == 0 || cols == 0) return ISING_OK;
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        proc_couplings<<<(rows + 127) / 128, 128, 0, st>>>(row0, rows, col0, cols, c, J_out);
+        DOCH_CUDA(cudaGetLastError());
+        DOCH_CUDA(cudaStreamSynchronize(st));
+        return ISING_OK;
+    });
 }

@@ -20,18 +20,20 @@ __global__ void cbrt_pair(const float *__restrict__ z, float *__restrict__ ours,
 
 extern "C" ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
                                               int32_t k, void *stream) {
-    using namespace doch;
-    if (!z || !ours || !ref || n < 0 || k < -40 || k > 40)
-        return fail(ISING_ERR_INVALID_ARG, "selftest_cbrt: bad argument");
-    if (n == 0) return ISING_OK;
-    int dev = 0, sms = 1;
-    DOCH_CUDA(cudaGetDevice(&dev));
-    DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 8LL * sms) blocks = 8LL * sms;
-    cbrt_pair<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        z, ours, ref, n, std::ldexp(1.0f, -3 * k), std::ldexp(1.0f, k));
-    DOCH_CUDA(cudaGetLastError());
-    DOCH_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    return ISING_OK;
+    return doch::guarded([&]() -> ising_status_t {
+        using namespace doch;
+        if (!z || !ours || !ref || n < 0 || k < -40 || k > 40)
+            return fail(ISING_ERR_INVALID_ARG, "selftest_cbrt: bad argument");
+        if (n == 0) return ISING_OK;
+        int dev = 0, sms = 1;
+        DOCH_CUDA(cudaGetDevice(&dev));
+        DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms) blocks = 8LL * sms;
+        cbrt_pair<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            z, ours, ref, n, std::ldexp(1.0f, -3 * k), std::ldexp(1.0f, k));
+        DOCH_CUDA(cudaGetLastError());
+        DOCH_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        return ISING_OK;
+    });
 }

@@ -193,3 +193,18 @@ def test_dense_values_in_fp8_bf16_and_float_types(lib):
     half[1, 2] = half[2, 1] = 0.5
     with pytest.raises(N.IsingError, match="UNSUPPORTED"):
         N.ising_default_params(N.Problem(half), eta=1.0, method=1)
+
+
+def test_host_exceptions_become_statuses(lib):
+    """A problem whose host copy cannot be allocated (a dense n = 2^31 matrix) returns
+    ISING_ERR_OOM from the C ABI instead of letting a C++ exception leave it."""
+    import ctypes
+    small = np.zeros(16, np.int8)
+    s = N.IsingProblem()
+    s.n, s.format, s.jtype = 1 << 31, N.FMT_DENSE, N.I8
+    s.dense = small.ctypes.data
+    a = np.zeros(1)
+    b = np.zeros(1)
+    st = lib.ising_default_params(ctypes.byref(s), 1.0, 1, a.ctypes.data, b.ctypes.data)
+    assert st == 6  # ISING_ERR_OOM
+    assert "allocation" in lib.ising_last_error().decode()
