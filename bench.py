@@ -53,6 +53,24 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(vals):
+    """Element-wise maximum of per-rank timings over the process group (the whole job is as slow
+    as its slowest rank); a single process returns its own values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(vals)
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(vals), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own units (weak scaling), timed by the slowest."""
+    return units_per_step * steps * world / seconds
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -906,11 +924,8 @@ def run_ours(args):
     N.ising_synchronize(wl.h, sid)
     elapsed = t_start.elapsed_time(t_end) / 1e3
     dom_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed, dom_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed, dom_s = tt.tolist()
-    value = wl.units * args.steps * world / elapsed
+    elapsed, dom_s = max_over_ranks([elapsed, dom_s])
+    value = job_rate(wl.units, args.steps, world, elapsed)
 
     # end to end through the C ABI with pinned host buffers
     n_e2e = max(1, min(args.steps, 3))
@@ -918,11 +933,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     e2e_t, h2d, d2h, how = wl.e2e(n_e2e, sid)
-    if world > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = tt.item()
-    e2e_val = wl.units * n_e2e * world / e2e_t
+    (e2e_t,) = max_over_ranks([e2e_t])
+    e2e_val = job_rate(wl.units, n_e2e, world, e2e_t)
     wl.close()
 
     if rank != 0:
