@@ -639,7 +639,9 @@ class Adoch:
         self.E = torch.zeros(1, dtype=torch.int64, device="cuda")
         self.units = float(self.n) * self.R * self.iters
         self.dominant_launches = self.iters  # one ADOCH step = pass + decide + update
-        self.launches = 3 * self.iters + 2 + 2
+        # step 0: pass + decide; steps 1..N-1: one pass (update and next terms) + boundary edges +
+        # decide; the last step: update only; readout: row_reduce + energy_finish
+        self.launches = 3 * self.iters + 2
         self.config = {"workload": f"ADOCH (Algorithm 2) on the torus2d {self.L}x{self.L} +-1 int8 lattice, FP32, "
                                    f"R=1, q={self.q}, {self.iters} steps + sign + int64 energy",
                        "n": self.n, "replicas": 1, "iters": self.iters, "q": self.q,
