@@ -125,8 +125,8 @@ typedef struct {
     int32_t format;          /* ising_format_t */
     int32_t jtype;           /* ising_dtype_t of the coupling values */
     const int64_t *row_ptr;  /* CSR: [n + 1] */
-    const int32_t *col;      /* CSR: [nnz] */
-    const void *val;         /* CSR: [nnz] */
+    const int32_t *col;      /* CSR: [nnz]; ELL: [n][ell_width] */
+    const void *val;         /* CSR: [nnz]; ELL: [n][ell_width] */
     int64_t l_rows, l_cols;  /* TORUS2D */
     const void *right;       /* TORUS2D: [l_rows][l_cols] */
     const void *down;        /* TORUS2D: [l_rows][l_cols] */
@@ -158,7 +158,8 @@ ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double e
  * Validate J and h (symmetry, zero diagonal, index ranges, finite values;
  * skipped with ISING_FLAG_SKIP_VALIDATION) and copy them to device memory
  * owned by a new handle. Dense couplings must be integers with |J| <= 256
- * (ISING_ERR_UNSUPPORTED otherwise, whatever their storage type); they are held in the tensor-core tile
+ * (ISING_ERR_UNSUPPORTED otherwise, whatever their storage type); they are
+ * held in the tensor-core tile
  * order, as packed 2-bit codes when every entry is -1, 0 or +1 and as BF16
  * otherwise (both exact). On failure *out is NULL.
  */
