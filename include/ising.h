@@ -159,9 +159,8 @@ ISING_API ising_status_t ising_default_params(const ising_problem_t *p, double e
  * skipped with ISING_FLAG_SKIP_VALIDATION) and copy them to device memory
  * owned by a new handle. Dense couplings must be integers with |J| <= 256
  * (ISING_ERR_UNSUPPORTED otherwise, whatever their storage type); they are
- * held in the tensor-core tile
- * order, as packed 2-bit codes when every entry is -1, 0 or +1 and as BF16
- * otherwise (both exact). On failure *out is NULL.
+ * held in the tensor-core tile order, as packed 2-bit codes when every entry
+ * is -1, 0 or +1 and as BF16 otherwise (both exact). On failure *out is NULL.
  */
 ISING_API ising_status_t ising_create(const ising_problem_t *p, int32_t flags, ising_handle_t *out);
 
