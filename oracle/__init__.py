@@ -14,11 +14,13 @@ What each part restates (arXiv 2509.01928):
   * ``procedural_rows`` -- rows of J x for J_ij = sin(i j + c) (Supplementary
                          Note 9), 1-based indices, J_ii = 0.
   * ``backward``      -- adjoint of N steps of Eq. FPE (derived; the paper has none).
+  * ``adjoint_along`` -- the same adjoint recursion along a given trajectory.
   * ``alpha_beta``    -- Eq. alphabeta; lambda_max by a dense symmetric
                          eigensolver, or by the Wigner estimate of Eq.
                          estimate_eig_J for n >= 1e4 (Supplementary Note 6).
   * ``adoch``         -- Algorithm 2 (ADOCH), Nesterov extrapolation with the
                          non-monotone acceptance test of Eq. BBscheme.
+  * ``tune_eta``      -- the choice of eta by probe iterations (Supplementary Note 6).
 
 Readings of the paper used here (where it is silent or ambiguous):
   * field h enters the convex part g, so T(x) = cbrt((Jx + alpha x + h)/beta);
@@ -93,6 +95,9 @@ def _load():
         lib.orc_backward.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int,
                                      _dp, _dp, _dp, _i64p]
         lib.orc_backward.restype = ctypes.c_int
+        lib.orc_adjoint_along.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                          _dp, _dp, _dp, _i64p]
+        lib.orc_adjoint_along.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -296,6 +301,46 @@ def backward(p: Problem, x0, alpha, beta: float, iters: int):
     return ga, gx, loss.value, zeros.value
 
 
+def adjoint_along_replica(p: Problem, xs, alpha, beta: float, R: int):
+    """The adjoint recursion of ``backward`` for ONE replica along a GIVEN
+    trajectory xs = (x^(0), ..., x^(N)) ([N+1][n], used as it is, in FP64)
+    instead of the oracle's own iterates. R is the replica count of the mean
+    in L. Returns (this replica's dL/dalpha [N], dL/dx^(0) [n], its share of
+    L, its count of components with x^(k+1) = 0)."""
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).ravel())
+    iters = a.size
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    assert xs.shape == (iters + 1, p.n)
+    ga = np.zeros(iters)
+    g1 = np.empty(p.n)
+    loss = ctypes.c_double(0.0)
+    zeros = ctypes.c_int64(0)
+    rc = _load().orc_adjoint_along(p.ref, int(R), _ptr(xs, _dp), _ptr(a, _dp), float(beta), iters,
+                                   _ptr(ga, _dp), _ptr(g1, _dp), ctypes.byref(loss), ctypes.byref(zeros))
+    if rc:
+        raise ValueError(f"orc_adjoint_along failed ({rc})")
+    return ga, g1, loss.value, zeros.value
+
+
+def adjoint_along(p: Problem, trajectory, alpha, beta: float, R: int | None = None):
+    """adjoint_along_replica for every replica of a trajectory [N+1][n][Rs]
+    (R defaults to Rs; a subset of a larger run passes the full count).
+    Returns (grad_alpha[N] summed over the replicas in replica order,
+    grad_x0[n][Rs], the replicas' share of L, zero_events)."""
+    t = np.asarray(trajectory)
+    Rs = t.shape[2]
+    R = Rs if R is None else int(R)
+    ga = np.zeros(t.shape[0] - 1)
+    gx = np.empty((p.n, Rs))
+    loss, zeros = 0.0, 0
+    for r in range(Rs):
+        g, gx[:, r], l, z = adjoint_along_replica(p, t[:, :, r], alpha, beta, R)
+        ga += g
+        loss += l
+        zeros += z
+    return ga, gx, loss, zeros
+
+
 # ---------------------------------------------------------------------------
 # parameter rule (Eq. alphabeta, Eq. estimate_eig_J, Supplementary Note 6)
 # ---------------------------------------------------------------------------
@@ -351,6 +396,34 @@ def alpha_beta(J, eta: float = 1.0, method: str = "auto"):
     alpha = eta * lam
     beta = float(n) ** 1.5 * (alpha + rowabs)
     return float(alpha), float(beta)
+
+
+def tune_eta(p: Problem, x0, etas, probe_iters: int, alpha1: float, beta1: float):
+    """Choice of eta in alpha = eta * lambda_max(-J) by a few probe iterations
+    (Supplementary Note 6: eta in (0, 2] is tuned by examining the Ising energy
+    over the first iterations, 5-10 for large graphs, 1-3 for ultra-large ones).
+
+    alpha1, beta1 are Eq. alphabeta at eta = 1 (alpha1 = lambda_max(-J));
+    since beta = n^1.5 (alpha + max_j sum_i |J_ij|) is affine in alpha, the
+    candidate eta has alpha = eta alpha1 and beta = beta1 + n^1.5 (eta - 1) alpha1.
+    For each candidate (in the given order): probe_iters DOCH steps from x0,
+    then the Ising energy of sign(x) per replica (exact int64 for integer J,
+    FP64 otherwise). Score = the best (lowest) energy over the replicas; the
+    chosen candidate has the lowest score, ties broken by the lower mean energy
+    and then by the earlier position. Returns (best[k], mean[k], index)."""
+    etas = [float(e) for e in etas]
+    n = float(p.n)
+    best, mean = [], []
+    for eta in etas:
+        a = eta * alpha1
+        b = beta1 + n ** 1.5 * (eta - 1.0) * alpha1
+        x = doch(p, x0, a, b, probe_iters)
+        s = sign(x)
+        E = energy_int(p, s)[0] if p.integer else energy(p, s)[0]
+        best.append(float(E.min()))
+        mean.append(float(np.mean(E.astype(np.float64))))
+    order = sorted(range(len(etas)), key=lambda k: (best[k], mean[k], k))
+    return np.array(best), np.array(mean), order[0]
 
 
 # ---------------------------------------------------------------------------

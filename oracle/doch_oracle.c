@@ -322,3 +322,51 @@ int orc_backward(const orc_problem *p, int R, const double *x0, const double *al
     free(xs); free(u); free(g); free(w);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * The same adjoint recursion (loss, g^N, then k = N-1 .. 0 as in
+ * orc_backward) for ONE replica along a GIVEN trajectory xs = x^(0..N)
+ * ([N+1][n], e.g. iterates computed in another precision), instead of the
+ * trajectory this file computes itself. R is the replica count of the mean
+ * in L (the loss and g^N carry 1/R). Adds this replica's dL/dalpha_k into
+ * grad_alpha [N], writes its dL/dx^0 into grad_x0 [n], adds its share of L
+ * into *loss and its count of components with x^(k+1) = 0 into *zero_events.
+ * ---------------------------------------------------------------------- */
+int orc_adjoint_along(const orc_problem *p, int R, const double *xs, const double *alpha,
+                      double beta, int iters, double *grad_alpha, double *grad_x0, double *loss,
+                      int64_t *zero_events)
+{
+    const int64_t n = p->n;
+    if (R < 1 || iters < 0 || beta <= 0.0) return 1;
+    double *u = (double *)malloc(sizeof(double) * (size_t)n);
+    double *g = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!u || !g || !w) { free(u); free(g); free(w); return 2; }
+    const double *xN = xs + (size_t)iters * n;
+    orc_coupling_product(p, 1, xN, u);
+    double lr = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double hi = p->h ? p->h[i] : 0.0;
+        lr += -0.5 * xN[i] * u[i] - hi * xN[i];
+        g[i] = -(u[i] + hi) / R;
+    }
+    *loss += lr / R;
+    int64_t zeros = 0;
+    for (int k = iters - 1; k >= 0; --k) {
+        const double *xk = xs + (size_t)k * n;
+        const double *xk1 = xs + (size_t)(k + 1) * n;
+        double ga = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (xk1[i] == 0.0) { w[i] = 0.0; ++zeros; }
+            else w[i] = g[i] / (3.0 * xk1[i] * xk1[i]);
+            ga += w[i] * xk[i];
+        }
+        grad_alpha[k] += ga / beta;
+        orc_coupling_product(p, 1, w, u);
+        for (int64_t i = 0; i < n; ++i) g[i] = (u[i] + alpha[k] * w[i]) / beta;
+    }
+    for (int64_t i = 0; i < n; ++i) grad_x0[i] = g[i];
+    if (zero_events) *zero_events += zeros;
+    free(u); free(g); free(w);
+    return 0;
+}

@@ -195,3 +195,55 @@ def test_adjoint_full_size_3regular_1e5():
     assert loss == pytest.approx(loss_r, rel=1e-5)
     assert _rel(ga, ga_r) <= 1e-3
     assert _rel(gx, gx_r) <= 1e-3
+
+
+def test_adjoint_fp32_full_size_along_the_device_trajectory():
+    """The stated configuration end to end in FP32: n = 1e5 random 3-regular
+    graph, +-1 couplings, R = 64, 200 FP32 iterations, checkpoint every 20.
+    An FP32 trajectory differs from the FP64 one where components pass near
+    zero, so the FP32 adjoint is checked against the FP64 oracle adjoint
+    replayed along the device's own FP32 trajectory: the trajectory comes from
+    200 single-step ising_iterate calls (bit-identical to one 200-step call,
+    which is the forward kernel ising_backward recomputes with), each of its
+    steps is checked against T in FP64 applied to the device's previous
+    iterate, and the gradients must agree within 1e-3 relative (the loss within
+    1e-6, the zero-crossing count exactly)."""
+    g = I.regular_pm1(100_000, 3, seed=5)
+    R, iters, ckpt = 64, 200, 20
+    x0 = I.x0_uniform(g.n, R, seed=5)
+    a0, beta = O.alpha_beta(g, eta=1.0, method="wigner")
+    alpha = np.full(iters, a0)
+    P = O.Problem(g)
+    h = N.ising_create(N.Problem(g))
+    traj = np.empty((R, iters + 1, g.n), np.float32)   # replica-major copy of x^(0..N)
+    try:
+        ga, gx, loss, ze = _gpu_backward(h, x0, alpha, beta, iters, ckpt)
+        x = torch.from_numpy(x0.copy()).cuda()
+        traj[:, 0, :] = x0.T
+        for k in range(iters):
+            N.ising_iterate(h, x, [a0], [beta], 1)
+            traj[:, k + 1, :] = x.cpu().numpy().T
+        x_all = torch.from_numpy(x0.copy()).cuda()
+        N.ising_iterate(h, x_all, [a0], [beta], iters)
+        assert np.array_equal(x_all.cpu().numpy().T, traj[:, iters, :])
+    finally:
+        N.ising_destroy(h)
+    for k in (0, 1, 50, iters - 1):                   # steps of the device trajectory are steps of T
+        xk = np.ascontiguousarray(traj[:, k, :].T, dtype=np.float64)
+        ref = O.doch(P, xk, a0, beta, 1)
+        got = traj[:, k + 1, :].T.astype(np.float64)
+        rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert rel.max() <= 1e-6, (k, rel.max())
+    ga_r = np.zeros(iters)
+    gx_r = np.empty((g.n, R))
+    loss_r, z_r = 0.0, 0
+    for r in range(R):
+        g_a, gx_r[:, r], l_r, z = O.adjoint_along_replica(P, traj[r], alpha, beta, R)
+        ga_r += g_a
+        loss_r += l_r
+        z_r += z
+    assert ze == z_r
+    assert loss == pytest.approx(loss_r, rel=1e-6)
+    assert _rel(ga, ga_r) <= 1e-3 and np.abs(ga - ga_r).max() <= 1e-3 * np.abs(ga_r).max()
+    rel_r = np.linalg.norm(gx - gx_r, axis=0) / np.linalg.norm(gx_r, axis=0)
+    assert rel_r.max() <= 1e-3, rel_r.max()

@@ -76,3 +76,26 @@ def test_doch_on_device_generated_problem():
     assert rel.max() <= 1e-10
     Er, _ = O.energy_int(O.Problem(J), O.sign(ref))
     assert np.array_equal(E, Er)
+
+
+@pytest.mark.parametrize("method, omethod, tol", [(1, "eig", 1e-6), (2, "wigner", 1e-12)])
+def test_device_params_match_oracle(method, omethod, tol):
+    """ising_params_device against the oracle's Eq. alphabeta: the power method
+    on the device against a dense symmetric eigensolver (to the power method's
+    convergence, 1e-6), the Wigner estimate of Eq. estimate_eig_J to 1e-12."""
+    J = I.s5_csr(1500, 3.0, seed=6)
+    ao, bo = O.alpha_beta(J, eta=1.0, method=omethod)
+    h = N.ising_create_s5(1500, 3.0, 6)
+    try:
+        da, db = N.ising_params_device(h, eta=1.0, method=method)
+    finally:
+        N.ising_destroy(h)
+    assert da[0] == pytest.approx(ao, rel=tol) and db[0] == pytest.approx(bo, rel=tol)
+    t = I.torus_pm1(48, 64, seed=7)
+    ao, bo = O.alpha_beta(t, eta=1.3, method=omethod)
+    h = N.ising_create(N.Problem(t))
+    try:
+        da, db = N.ising_params_device(h, eta=1.3, method=method)
+    finally:
+        N.ising_destroy(h)
+    assert da[0] == pytest.approx(ao, rel=tol) and db[0] == pytest.approx(bo, rel=tol)

@@ -504,3 +504,78 @@ def test_stopping_rule_definition():
     x1, s1, _ = O.doch_until(p, x0, alpha, beta, 30, 1e9)
     np.testing.assert_array_equal(x1, O.doch(p, x0, alpha, beta, 1))
     assert (s1 == 1).all()
+
+
+def test_adjoint_along_a_given_trajectory():
+    """adjoint_along runs the recursion on the iterates it is given: on the
+    oracle's own FP64 trajectory it reproduces backward bit for bit, and on
+    an FP32-rounded trajectory (not a fixed orbit of T) it matches the
+    forward-mode products M_k = diag(1/(3 (x^(k+1))^2)) (J + alpha_k I)/beta,
+    m_k = x^k / (3 (x^(k+1))^2 beta) formed along that same trajectory."""
+    n, N, R = 9, 6, 3
+    J = _sk(n, seed=33)
+    h = 0.2 * I.gaussian(I.stream_seed(33, 1), I.stream_seed(33, 2), 0, n)
+    p = O.Problem(J, h)
+    alpha0, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    beta /= 10
+    alpha = alpha0 * (1.0 + 0.07 * np.cos(np.arange(N)))
+    x0 = I.x0_uniform(n, R, seed=34, dtype=np.float64)
+    traj = [x0]
+    for k in range(N):
+        traj.append(O.doch(p, traj[-1], alpha[k], beta, 1))
+    ga, gx, loss, z = O.backward(p, x0, alpha, beta, N)
+    ga2, gx2, loss2, z2 = O.adjoint_along(p, np.array(traj), alpha, beta)
+    assert np.array_equal(ga, ga2) and np.array_equal(gx, gx2) and loss == loss2 and z == z2 == 0
+    t32 = [t.astype(np.float32).astype(np.float64) for t in traj]
+    ga3, gx3, loss3, _ = O.adjoint_along(p, np.array(t32), alpha, beta, R=5)
+    ga_ref = np.zeros(N)
+    loss_ref = 0.0
+    for r in range(R):
+        xs = [t[:, r] for t in t32]
+        loss_ref += (-0.5 * xs[N] @ (J @ xs[N]) - h @ xs[N]) / 5
+        gN = -(J @ xs[N] + h) / 5
+        M = [np.diag(1 / (3 * xs[k + 1] ** 2)) @ (J + alpha[k] * np.eye(n)) / beta for k in range(N)]
+        m = [xs[k] / (3 * xs[k + 1] ** 2) / beta for k in range(N)]
+        P = np.eye(n)
+        for k in range(N):
+            P = M[k] @ P
+        np.testing.assert_allclose(gx3[:, r], P.T @ gN, rtol=1e-10, atol=1e-14)
+        for k in range(N):
+            Q = np.eye(n)
+            for j in range(k + 1, N):
+                Q = M[j] @ Q
+            ga_ref[k] += gN @ (Q @ m[k])
+    np.testing.assert_allclose(ga3, ga_ref, rtol=1e-10)
+    assert loss3 == pytest.approx(loss_ref, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# eta tuning by probe iterations (Supplementary Note 6)
+# ---------------------------------------------------------------------------
+
+def test_tune_eta_beta_rule_and_selection():
+    """The candidates' beta (affine in alpha) equals Eq. alphabeta evaluated directly at each
+    eta; the chosen eta's score is the minimum over the candidates; a candidate list of one
+    eta reduces to a plain DOCH run and its energies; and on a 12-spin instance whose
+    brute-force ground energy some candidate reaches, the chosen score is that ground energy."""
+    g = I.erdos_renyi_pm1(12, 0.5, seed=35)
+    P = O.Problem(g)
+    a1, b1 = O.alpha_beta(g, eta=1.0, method="eig")
+    for eta in (0.3, 1.0, 1.7):
+        a, b = O.alpha_beta(g, eta=eta, method="eig")
+        assert a == pytest.approx(eta * a1, rel=1e-14)
+        assert b == pytest.approx(b1 + 12 ** 1.5 * (eta - 1.0) * a1, rel=1e-14)
+    x0 = I.x0_uniform(12, 16, seed=36, dtype=np.float64)
+    etas = [0.1, 0.4, 0.7, 1.0, 1.3, 1.6, 2.0]
+    best, mean, k = O.tune_eta(P, x0, etas, 40, a1, b1)
+    assert best[k] == best.min()
+    assert all(mean[k] <= mean[j] for j in range(len(etas)) if best[j] == best[k])
+    b_one, m_one, k_one = O.tune_eta(P, x0, [0.7], 40, a1, b1)
+    a, b = O.alpha_beta(g, eta=0.7, method="eig")
+    E = O.energy_int(P, O.sign(O.doch(P, x0, a, b, 40)))[0]
+    assert k_one == 0 and b_one[0] == E.min() and m_one[0] == pytest.approx(E.mean(), rel=1e-15)
+    S = _all_spins(12).astype(np.int64)
+    Jd = g.to_dense().astype(np.int64)
+    ground = int((-(S @ Jd * S).sum(axis=1) // 2).min())   # brute force over all 2^12 states
+    assert best.min() >= ground
+    assert best[k] == ground, (best, ground)
