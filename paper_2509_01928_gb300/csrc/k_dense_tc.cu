@@ -46,6 +46,7 @@
 
 #include "cbrt.cuh"
 #include "internal.cuh"
+#include "mbar.cuh"
 
 namespace doch {
 namespace {
@@ -56,7 +57,6 @@ template <bool TERN> constexpr int kStagesOf = TERN ? 6 : 4;
 constexpr int kBM = 128;           // rows of J per tile (MMA M)
 constexpr int kBK = 64;            // K per stage: 64 BF16 = 128 bytes = one swizzle row
 constexpr int kThreadsTC = 256;
-constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
 
 constexpr uint32_t kTernTile = kBM * kBK / 4;  // bytes of one packed ternary J tile (2 bits per entry)
 constexpr int kJStages = 8;                      // packed ternary tiles staged ahead
@@ -76,70 +76,6 @@ struct DenseSmem {
     uint32_t tmem_base;
     int abort_flag;
 };
-
-__device__ __forceinline__ uint32_t saddr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for a long phase (the accumulator): polls every ~0.5 us so the
-// waiting warps leave the issue slots to the producer, MMA and converter threads
-__device__ __forceinline__ bool mbar_wait_idle(unsigned long long *bar, uint32_t parity, int *err,
-                                               volatile int *abort_flag) {
-    const uint64_t t0 = gtime();
-    while (!mbar_test(bar, parity)) {
-        if (*abort_flag) return false;
-        if (gtime() - t0 > kWaitNs) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            *abort_flag = 1;
-            return false;
-        }
-        __nanosleep(500);
-    }
-    return true;
-}
-
-// bounded wait on a phase parity; false (and the error word set) on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *err,
-                                          volatile int *abort_flag) {
-    if (mbar_test(bar, parity)) return true;
-    const uint64_t t0 = gtime();
-    while (true) {
-        if (mbar_test(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtime() - t0 > kWaitNs) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
 
 // contiguous global -> shared copy (16-byte aligned, size a multiple of 16)
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {

@@ -37,3 +37,36 @@ extern "C" ising_status_t ising_selftest_cbrt(const float *z, float *ours, float
         return ISING_OK;
     });
 }
+
+// ---------------------------------------------------------------------------
+// Bounded-wait self-test: one thread waits on a shared-memory mbarrier with
+// the same bounded wait the tensor-core kernel uses. With arrive = 0 nobody
+// arrives, so the wait runs out after limit_ns and sets DEV_ERR_TIMEOUT in the
+// handle's error word; with arrive = 1 the thread arrives first and the wait
+// completes at once. Nothing else is touched, so the context stays usable.
+// ---------------------------------------------------------------------------
+#include "mbar.cuh"
+
+namespace doch {
+namespace {
+
+__global__ void wait_selftest(int *err, int arrive, uint64_t limit_ns) {
+    __shared__ alignas(8) unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bar)) : "memory");
+    mbar_wait(&bar, 0, err, &abort_flag, limit_ns);
+}
+
+}  // namespace
+
+ising_status_t selftest_wait_launch(int *err, bool arrive, uint64_t limit_ns, cudaStream_t st) {
+    wait_selftest<<<1, 32, 0, st>>>(err, arrive ? 1 : 0, limit_ns);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+}  // namespace doch
