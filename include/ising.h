@@ -230,8 +230,10 @@ ISING_API void ising_destroy(ising_handle_t h);
  *          H(x^(k)) of Eq. Hamilton (with -h^T x for a field), each with the
  *          alpha of step k (the last step's for k = iters). Computed in FP64
  *          on the device, fused into the iteration kernel.
- * For DENSE the iterate is BF16 and the coupling product runs on the
- * tcgen05 tensor cores with FP32 accumulation. For PROCEDURAL the iterate is
+ * For DENSE a BF16 iterate runs the coupling product on the tcgen05 tensor
+ * cores (FP32 accumulation, BF16 state); an F32 iterate runs the plain FP32
+ * form (FP32 products and accumulation on the CUDA cores, FP32 state, CUDA's
+ * cbrtf), the reference the BF16 form is compared with. For PROCEDURAL the iterate is
  * F32 and each step generates the couplings; an H_trace costs one more
  * coupling product per step.
  */
@@ -308,6 +310,31 @@ ISING_API ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t x
                             int32_t *best, int8_t *spins, void *stream);
 
 /*
+ * Choice of eta in alpha = eta * lambda_max(-J) by probe iterations
+ * (Supplementary Note 6: eta in (0, 2] is tuned by examining the Ising energy
+ * over the first few iterations -- 5 to 10 for large graphs, 1 to 3 for
+ * ultra-large ones). For a one-instance handle:
+ *   alpha1, beta1  Eq. alphabeta at eta = 1 (from ising_default_params or
+ *          ising_params_device); beta is affine in alpha, so candidate k uses
+ *          alpha_k = etas[k] alpha1 and beta_k = beta1 + n^1.5 (etas[k] - 1) alpha1.
+ *   x0     [n][R] start of every probe (xtype as ising_iterate accepts for the
+ *          handle's format; host or device); not modified.
+ * For each candidate in order: probe_iters DOCH steps from x0 (ising_iterate),
+ * then the Ising energies of sign(x) per replica (exact int64 for integer J,
+ * FP64 otherwise, as ising_energy). score_best[k] = the lowest energy over the
+ * replicas, score_mean[k] = the mean energy; the chosen candidate has the
+ * lowest score_best (ties: lower score_mean, then the earlier candidate).
+ *   score_best, score_mean  [n_etas] FP64 or NULL;  best_index int32 or NULL;
+ *   alpha_out, beta_out     the chosen candidate's alpha and beta, or NULL.
+ * Outputs may be host or device pointers. n_etas 1 .. 4096. The handle keeps
+ * two iterate-sized scratch buffers for the probes. Synchronises the stream.
+ */
+ISING_API ising_status_t ising_tune_eta(ising_handle_t h, const void *x0, int32_t xtype, int32_t R,
+                                        const double *etas, int32_t n_etas, int32_t probe_iters, double alpha1,
+                                        double beta1, double *score_best, double *score_mean, int32_t *best_index,
+                                        double *alpha_out, double *beta_out, void *stream);
+
+/*
  * Adjoint of `iters` DOCH steps (derived from Eq. FPE; the paper has no
  * gradients). Loss: the mean relaxed energy of the final iterates,
  *   L = (1/R) sum_r ( -1/2 x_r^T J x_r - h^T x_r ) at x^(iters)
@@ -357,9 +384,12 @@ ISING_API ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n
  * -1/2 s_r^T J s_r and cut_r with W = -2J exactly in int64, as ising_energy.
  *
  * Its reduction partials live in a fixed device array inside the library
- * (196,608 bytes, held on every device that loads the library until the
- * process exits), so R is limited to 8192; larger R fails with
- * ISING_ERR_INVALID_ARG. The first call on a device looks up that array's
+ * (131,072 bytes: two int64 per (replica, chunk of sites), held on every
+ * device that loads the library until the process exits), so R is limited
+ * to 8192; larger R fails with ISING_ERR_INVALID_ARG. Every array must be
+ * memory of the current device; the library cannot check their lengths, so
+ * the caller guarantees right/down hold l_rows * l_cols values, x
+ * l_rows * l_cols * R and each given output R. The first call on a device looks up that array's
  * address (cudaGetSymbolAddress, with the device current) and caches it;
  * make that first call before any stream capture. Every call shares the
  * array: two calls whose work overlaps on the GPU (different streams, or
@@ -391,6 +421,19 @@ ISING_API ising_status_t ising_selftest_cbrt(const float *z, float *ours, float 
  */
 ISING_API ising_status_t ising_selftest_procedural(int64_t row0, int32_t rows, int64_t col0, int32_t cols,
                                                    int64_t c, float *J_out, void *stream);
+
+/*
+ * Diagnostic of the failure path of bounded device waits (the paper has no
+ * counterpart): launches one thread that waits on a shared-memory mbarrier
+ * with the bounded wait the tensor-core kernel uses, limit limit_ns
+ * (1e3 .. 1e9 ns). With arrive = 0 nothing ever arrives, the wait gives up
+ * after the limit, sets the timeout bit of the handle's device error word,
+ * and the call returns ISING_ERR_TIMEOUT; the error word is then cleared and
+ * the handle stays usable. With arrive != 0 the thread arrives first and the
+ * call returns ISING_OK. No trap, no fault: the kernel simply returns.
+ * Synchronises the stream.
+ */
+ISING_API ising_status_t ising_selftest_wait(ising_handle_t h, int32_t arrive, int64_t limit_ns, void *stream);
 
 /* Static description of a status code. */
 ISING_API const char *ising_status_string(ising_status_t s);

@@ -91,6 +91,11 @@ def load():
     lib.ising_selftest_procedural.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int64, _vp, _vp]
     lib.ising_selftest_procedural.restype = ctypes.c_int
+    lib.ising_tune_eta.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.ising_tune_eta.restype = ctypes.c_int
+    lib.ising_selftest_wait.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, _vp]
+    lib.ising_selftest_wait.restype = ctypes.c_int
     lib.ising_status_string.argtypes = [ctypes.c_int]
     lib.ising_status_string.restype = ctypes.c_char_p
     lib.ising_last_error.argtypes = []
@@ -353,6 +358,21 @@ def ising_energy(handle: int, x, E_int=None, cut_int=None, E_f64=None, cut_f64=N
                                _stream(stream, x, E_int, E_f64)), "ising_energy")
 
 
+def ising_tune_eta(handle: int, x0, etas, probe_iters: int, alpha1: float, beta1: float, stream=None):
+    """eta by probe iterations (Supplementary Note 6): returns (alpha, beta, index, score_best[k],
+    score_mean[k]) of the chosen candidate among etas, all starts in x0 ([n][R] or [n])."""
+    R = 1 if x0.ndim == 1 else int(x0.shape[1])
+    e = _f64(etas)
+    k = e.size
+    best, mean = np.zeros(k), np.zeros(k)
+    idx = np.zeros(1, np.int32)
+    a, b = np.zeros(1), np.zeros(1)
+    _check(load().ising_tune_eta(handle, _ptr(x0), _dtype_code(x0), R, e.ctypes.data, k, int(probe_iters),
+                                 float(alpha1), float(beta1), best.ctypes.data, mean.ctypes.data, idx.ctypes.data,
+                                 a.ctypes.data, b.ctypes.data, _stream(stream, x0)), "ising_tune_eta")
+    return float(a[0]), float(b[0]), int(idx[0]), best, mean
+
+
 def ising_backward(handle: int, x0, alpha, beta: float, iters: int, ckpt_every: int,
                    grad_alpha=None, grad_x0=None, loss=None, zero_events=None, stream=None):
     """Adjoint of `iters` DOCH steps into the given output arrays."""
@@ -365,12 +385,46 @@ def ising_backward(handle: int, x0, alpha, beta: float, iters: int, ckpt_every: 
 
 
 def ising_energy_torus_noalloc(right, down, x, E_out=None, cut_out=None, stream=None):
-    """Lattice energy/cut from device arrays, with no device allocation (see include/ising.h)."""
+    """Lattice energy/cut from device arrays, with no device allocation (see include/ising.h).
+
+    The C entry point cannot see array lengths, so the arguments are checked here before
+    the call: right and down int8 torch tensors of one 2-D shape [l_rows][l_cols]; x a
+    float32 tensor [n] or [n][R] with n = l_rows * l_cols; E_out and cut_out int64 tensors
+    of at least R elements; all contiguous CUDA tensors on x's device (the call runs with
+    that device current). ValueError otherwise."""
+    import torch
+
+    def need(cond, msg):
+        if not cond:
+            raise ValueError(f"ising_energy_torus_noalloc: {msg}")
+
+    for name, t in (("right", right), ("down", down), ("x", x), ("E_out", E_out), ("cut_out", cut_out)):
+        need(t is None or isinstance(t, torch.Tensor), f"{name} must be a torch tensor")
+    need(E_out is not None or cut_out is not None, "give E_out, cut_out or both")
+    need(right.dtype == torch.int8 and down.dtype == torch.int8, "right and down must be int8")
+    need(right.dim() == 2 and tuple(down.shape) == tuple(right.shape), "right and down must share one 2-D shape")
     lr, lc = int(right.shape[0]), int(right.shape[1])
-    R = 1 if x.ndim == 1 else int(x.shape[1])
-    _check(load().ising_energy_torus_noalloc(_ptr(right), _ptr(down), lr, lc, _ptr(x), R,
-                                             _ptr(E_out), _ptr(cut_out), _stream(stream, x)),
-           "ising_energy_torus_noalloc")
+    need(x.dtype == torch.float32, "x must be float32")
+    need(x.dim() in (1, 2) and int(x.shape[0]) == lr * lc, "x must be [l_rows * l_cols] or [l_rows * l_cols][R]")
+    R = 1 if x.dim() == 1 else int(x.shape[1])
+    for name, t in (("E_out", E_out), ("cut_out", cut_out)):
+        if t is not None:
+            need(t.dtype == torch.int64 and t.numel() >= R, f"{name} must be int64 with at least R = {R} elements")
+    tensors = [t for t in (right, down, x, E_out, cut_out) if t is not None]
+    need(all(t.is_contiguous() for t in tensors), "every tensor must be contiguous")
+    need(all(t.is_cuda for t in tensors), "every tensor must be a CUDA tensor")
+    need(all(t.device == x.device for t in tensors), "every tensor must be on x's device")
+    with torch.cuda.device(x.device):
+        _check(load().ising_energy_torus_noalloc(_ptr(right), _ptr(down), lr, lc, _ptr(x), R,
+                                                 _ptr(E_out), _ptr(cut_out), _stream(stream, x)),
+               "ising_energy_torus_noalloc")
+
+
+def ising_selftest_wait(handle: int, arrive: bool, limit_ns: int, stream=None):
+    """One bounded mbarrier wait of limit_ns on the device (see include/ising.h): raises
+    IsingError(ISING_ERR_TIMEOUT) when nothing arrives."""
+    _check(load().ising_selftest_wait(handle, 1 if arrive else 0, int(limit_ns), _stream(stream)),
+           "ising_selftest_wait")
 
 
 def ising_synchronize(handle: int, stream=None):

@@ -430,6 +430,7 @@ ising_status_t finish(ising_context *c, cudaStream_t st, bool must_sync) {
 
 void destroy_ctx(ising_context *c) {
     if (!c) return;
+    c->tune.release();
     cudaFree(c->inst_off);
     cudaFree(c->row_ptr);
     cudaFree(c->col);
@@ -987,6 +988,18 @@ ising_status_t ising_csr_export(ising_handle_t h, int64_t *row_ptr, int32_t *col
 
 void ising_destroy(ising_handle_t h) { destroy_ctx(h); }
 
+ising_status_t ising_selftest_wait(ising_handle_t h, int32_t arrive, int64_t limit_ns, void *stream) {
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
+        if (limit_ns < 1000 || limit_ns > 1000000000LL)
+            return fail(ISING_ERR_INVALID_ARG, "limit_ns must be in 1e3 .. 1e9");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        DOCH_CHECK(selftest_wait_launch(h->err_word, arrive != 0, static_cast<uint64_t>(limit_ns), st));
+        return finish(h, st, true);
+    });
+}
+
 ising_status_t ising_get_size(ising_handle_t h, int64_t *n, int32_t *n_instances) {
     return doch::guarded([&]() -> ising_status_t {
         if (!h) return fail(ISING_ERR_INVALID_ARG, "handle is NULL");
@@ -1012,7 +1025,8 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
         if (R < 1 || iters < 0) return fail(ISING_ERR_INVALID_ARG, "R must be >= 1 and iters >= 0");
         if (alpha_len != 1 && alpha_len != iters) return fail(ISING_ERR_INVALID_ARG, "alpha_len must be 1 or iters");
         if (h->format == ISING_FMT_DENSE) {
-            if (xtype != ISING_BF16) return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16");
+            if (xtype != ISING_BF16 && xtype != ISING_F32)
+                return fail(ISING_ERR_INVALID_ARG, "DENSE iterates are BF16 (tensor cores) or F32 (plain FP32 form)");
         } else if (h->format == ISING_FMT_PROCEDURAL) {
             if (xtype != ISING_F32) return fail(ISING_ERR_INVALID_ARG, "PROCEDURAL iterates are F32");
         } else if (xtype != ISING_F32 && xtype != ISING_F64) {
@@ -1051,7 +1065,11 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
         if (c->format == ISING_FMT_DENSE) {
             if (H_trace) return fail(ISING_ERR_UNSUPPORTED, "H trace is not available for DENSE couplings");
             if (c->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "DENSE runs one instance");
-            if (iters > 0) DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
+            if (iters > 0 && xtype == ISING_BF16)
+                DOCH_CHECK(dense_iterate(c, xd, R, alpha_h.data(), alpha_len, beta_h[0], iters, st));
+            if (iters > 0 && xtype == ISING_F32)
+                DOCH_CHECK(dense_iterate_f32(c, static_cast<float *>(xd), R, alpha_h.data(), alpha_len, beta_h[0],
+                                             iters, st));
             done = true;
         }
         if (!done && !H_trace && c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && iters > 0) {
@@ -1332,6 +1350,91 @@ ising_status_t ising_energy(ising_handle_t h, const void *x, int32_t xtype, int3
             }
         }
         return finish(c, st, must_sync);
+    });
+}
+
+ising_status_t ising_tune_eta(ising_handle_t h, const void *x0, int32_t xtype, int32_t R, const double *etas,
+                              int32_t n_etas, int32_t probe_iters, double alpha1, double beta1, double *score_best,
+                              double *score_mean, int32_t *best_index, double *alpha_out, double *beta_out,
+                              void *stream) {
+    return doch::guarded([&]() -> ising_status_t {
+        g_err.clear();
+        if (!h || !x0 || !etas) return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+        ising_context *c = h;
+        if (c->n_inst != 1) return fail(ISING_ERR_UNSUPPORTED, "ising_tune_eta runs on one instance");
+        if (R < 1 || R > 65535 || n_etas < 1 || n_etas > 4096 || probe_iters < 0)
+            return fail(ISING_ERR_INVALID_ARG, "need 1 <= R <= 65535, 1 <= n_etas <= 4096, probe_iters >= 0");
+        if (!std::isfinite(alpha1) || !std::isfinite(beta1) || beta1 <= 0.0)
+            return fail(ISING_ERR_INVALID_ARG, "alpha1 and beta1 must be finite, beta1 > 0");
+        std::vector<double> eta_h(n_etas);
+        {
+            std::vector<unsigned char> tmp;
+            DOCH_CHECK(to_host(etas, sizeof(double) * n_etas, tmp));
+            std::memcpy(eta_h.data(), tmp.data(), tmp.size());
+        }
+        const double n15 = std::pow(static_cast<double>(c->n), 1.5);
+        std::vector<double> a_h(n_etas), b_h(n_etas);
+        for (int k = 0; k < n_etas; ++k) {
+            if (!std::isfinite(eta_h[k])) return fail(ISING_ERR_NONFINITE, "eta is not finite");
+            a_h[k] = eta_h[k] * alpha1;
+            b_h[k] = beta1 + n15 * (eta_h[k] - 1.0) * alpha1;   // beta is affine in alpha (Eq. alphabeta)
+            if (!(b_h[k] > 0.0)) return fail(ISING_ERR_INVALID_ARG, "beta of a candidate eta is not > 0");
+        }
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const size_t xbytes = static_cast<size_t>(c->n) * R * xtype_size(xtype);
+        const size_t eb = ((sizeof(double) * static_cast<size_t>(R) * n_etas + 255) / 256) * 256;
+        const size_t xoff = 2 * eb;
+        DOCH_CHECK(c->tune.ensure(xoff + 2 * xbytes));
+        unsigned char *base = c->tune.as<unsigned char>();
+        int64_t *Ei = reinterpret_cast<int64_t *>(base);       // [n_etas][R] (integer J)
+        double *Ed = reinterpret_cast<double *>(base + eb);     // [n_etas][R]
+        void *x0d = base + xoff;                                // the start, kept for every candidate
+        void *xw = base + xoff + xbytes;                        // the probe iterate
+        DOCH_CUDA(cudaMemcpyAsync(x0d, x0, xbytes, cudaMemcpyDefault, st));
+        const bool integer = c->integer;
+        for (int k = 0; k < n_etas; ++k) {
+            DOCH_CUDA(cudaMemcpyAsync(xw, x0d, xbytes, cudaMemcpyDeviceToDevice, st));
+            DOCH_CHECK(ising_iterate(h, xw, xtype, R, &a_h[k], 1, &b_h[k], probe_iters, nullptr, stream));
+            DOCH_CHECK(ising_energy(h, xw, xtype, R, integer ? Ei + static_cast<size_t>(k) * R : nullptr, nullptr,
+                                    integer ? nullptr : Ed + static_cast<size_t>(k) * R, nullptr, nullptr, nullptr,
+                                    stream));
+        }
+        std::vector<int64_t> Ei_h(integer ? static_cast<size_t>(n_etas) * R : 0);
+        std::vector<double> Ed_h(static_cast<size_t>(n_etas) * R);
+        if (integer) {
+            DOCH_CUDA(cudaMemcpyAsync(Ei_h.data(), Ei, sizeof(int64_t) * Ei_h.size(), cudaMemcpyDeviceToHost, st));
+        } else {
+            DOCH_CUDA(cudaMemcpyAsync(Ed_h.data(), Ed, sizeof(double) * Ed_h.size(), cudaMemcpyDeviceToHost, st));
+        }
+        DOCH_CHECK(finish(c, st, true));
+        if (integer)
+            for (size_t t = 0; t < Ei_h.size(); ++t) Ed_h[t] = static_cast<double>(Ei_h[t]);
+        // score = best energy over the replicas; ties: lower mean, then the earlier candidate
+        std::vector<double> best(n_etas), mean(n_etas);
+        int pick = 0;
+        for (int k = 0; k < n_etas; ++k) {
+            const double *e = Ed_h.data() + static_cast<size_t>(k) * R;
+            double mn = e[0], sum = 0.0;
+            long long isum = 0;
+            for (int r = 0; r < R; ++r) {
+                mn = std::min(mn, e[r]);
+                if (integer) isum += Ei_h[static_cast<size_t>(k) * R + r];
+                else sum += e[r];
+            }
+            best[k] = mn;
+            mean[k] = (integer ? static_cast<double>(isum) : sum) / R;
+            if (best[k] < best[pick] || (best[k] == best[pick] && mean[k] < mean[pick])) pick = k;
+        }
+        auto put = [&](void *dst, const void *src, size_t bytes) -> ising_status_t {
+            if (dst) DOCH_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+            return ISING_OK;
+        };
+        DOCH_CHECK(put(score_best, best.data(), sizeof(double) * n_etas));
+        DOCH_CHECK(put(score_mean, mean.data(), sizeof(double) * n_etas));
+        DOCH_CHECK(put(best_index, &pick, sizeof(int32_t)));
+        DOCH_CHECK(put(alpha_out, &a_h[pick], sizeof(double)));
+        DOCH_CHECK(put(beta_out, &b_h[pick], sizeof(double)));
+        return ISING_OK;
     });
 }
 

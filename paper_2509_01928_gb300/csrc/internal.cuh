@@ -71,6 +71,10 @@ struct BatchedConfig {
     int ctas_per_sm = 2;
 };
 
+// Bounded-wait self-test (k_selftest.cu): one mbarrier wait of limit_ns that
+// nobody satisfies (arrive = false) or that is satisfied at once.
+ising_status_t selftest_wait_launch(int *err, bool arrive, uint64_t limit_ns, cudaStream_t st);
+
 }  // namespace doch
 
 // the opaque handle of the C ABI
@@ -130,6 +134,7 @@ struct ising_context {
     doch::DevBuf params;    // alpha/beta tables on the device
     doch::DevBuf ckpt;      // checkpoints of the adjoint
     doch::DevBuf work;      // misc. work space
+    doch::DevBuf tune;      // eta tuning: the probe iterate and its energies
     int *err_word = nullptr;  // device error word
     int *err_host = nullptr;  // pinned mirror
     int *count_host = nullptr;  // pinned: running-pair count of the stopping rule
@@ -263,6 +268,10 @@ ising_status_t dense_iterate(ising_context *c, void *x, int R, const double *alp
                              double beta, int iters, cudaStream_t st);
 ising_status_t dense_energy(ising_context *c, const void *x, int xtype, int R, int64_t *E_i, int64_t *cut_i,
                             double *E_d, double *cut_d, cudaStream_t st);
+// Dense couplings, plain FP32 form on the CUDA cores (k_dense_f32.cu): FP32
+// iterates [n][R] updated in place, FP32 products and accumulation.
+ising_status_t dense_iterate_f32(ising_context *c, float *x, int R, const double *alpha_h, int alpha_len,
+                                 double beta, int iters, cudaStream_t st);
 
 // Procedural couplings (k_proc.cu), FP32 iterates, one instance, no field.
 // One DOCH step x_out = T(x_in); energies into E_d / cut_d (device, R each);
@@ -291,5 +300,9 @@ ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int nu
 ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
                                      const double *lpart, int lblocks, int R, double *grad_alpha,
                                      double *loss, cudaStream_t st);
+
+// Bounded-wait self-test (k_selftest.cu): one mbarrier wait of limit_ns that
+// nobody satisfies (arrive = false) or that is satisfied at once.
+ising_status_t selftest_wait_launch(int *err, bool arrive, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace doch
