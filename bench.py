@@ -307,7 +307,8 @@ class Dense:
         self.config = {"workload": f"dense {self.n}x{self.n} +-1 (BF16, exact), R={self.R} BF16 replicas, "
                                    f"{self.iters} DOCH iterations on tcgen05 + exact int64 energy/cut",
                        "n": self.n, "replicas": self.R, "iters": self.iters,
-                       "l2": "J (537 MB) larger than L2; no flush"}
+                       "l2": "J held as 67 MB of packed 2-bit codes (L2-resident across iterations); the BF16 "
+                             "iterates (8.4 MB each) too; no flush"}
 
     def step(self, sid, stream, ev_a=None, ev_b=None):
         N = self.N
@@ -354,6 +355,120 @@ class Dense:
         dt = time.perf_counter() - t0
         return {"value": n * 2 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"dense {n}x{n} +-1, 2 replicas, 2 FP64 DOCH iterations"}
+
+    def close(self):
+        self.N.ising_destroy(self.h)
+
+
+class Precision:
+    """The low-precision form against the plain FP32 form on one dense instance (n = 16384, J = +-1,
+    R = 256 replicas from the same seeded start): BF16 iterates with the coupling product on the
+    tcgen05 tensor cores (the timed step: 1000 DOCH iterations + exact energy) next to FP32 iterates
+    with FP32 products on the CUDA cores. After the timed loop both forms run the same iteration
+    count from the same start, recording the integer energies of all replicas every `stride`
+    iterations; the line reports each form's spin-updates/s, its final energy distribution (best,
+    mean, std over the replicas) and the iterations and time each form needs to bring its mean
+    energy within `tol` of the FP32 form's final mean ("equal final energy")."""
+
+    dominant = "dense_tc_kernel"
+    dtype = "bf16"
+
+    def __init__(self, args, rank, N, I, torch):
+        self.n, self.R, self.iters = args.dense_n, 256, args.dense_iters
+        J = I.dense_pm1(self.n, seed=3 + 1000 * rank)
+        self.x0 = I.x0_uniform(self.n, self.R, seed=3 + 1000 * rank)
+        prob = N.Problem(J)
+        self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
+        self.h = N.ising_create(prob, flags=N.FLAG_ASYNC)
+        self.N, self.torch = N, torch
+        self.x0_f32 = torch.from_numpy(self.x0).cuda()
+        self.x0_bf16 = self.x0_f32.to(torch.bfloat16)
+        self.x0_d = self.x0_bf16
+        self.x = torch.empty_like(self.x0_bf16)
+        self.E = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        self.units = float(self.n) * self.R * self.iters
+        self.dominant_launches = self.iters
+        self.launches = self.iters + 2 + 4
+        self.stride, self.tol = args.precision_stride, args.precision_tol
+        self.config = {"workload": f"dense {self.n}x{self.n} +-1, R={self.R}: BF16 tensor-core form "
+                                   f"({self.iters} DOCH iterations + exact energy, timed) against the plain "
+                                   f"FP32 CUDA-core form at equal final energy",
+                       "n": self.n, "replicas": self.R, "iters": self.iters,
+                       "l2": "J held as 67 MB of packed 2-bit codes (L2-resident); no flush"}
+
+    def step(self, sid, stream, ev_a=None, ev_b=None):
+        N = self.N
+        self.x.copy_(self.x0_bf16)
+        if ev_a is not None:
+            ev_a.record(stream)
+        N.ising_iterate(self.h, self.x, self.alpha, self.beta, self.iters, stream=sid)
+        if ev_b is not None:
+            ev_b.record(stream)
+        N.ising_energy(self.h, self.x, E_int=self.E, stream=sid)
+
+    def _form(self, x0, sid, stream):
+        """One uninterrupted run of `iters` iterations (CUDA events) and the energy trajectory of a
+        chunked run from the same start (untimed)."""
+        N, torch = self.N, self.torch
+        x = x0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        N.ising_iterate(self.h, x, self.alpha, self.beta, self.iters, stream=sid)
+        e1.record(stream)
+        N.ising_synchronize(self.h, sid)
+        sec = e0.elapsed_time(e1) / 1e3
+        x = x0.clone()
+        E = torch.zeros(self.R, dtype=torch.int64, device="cuda")
+        traj = []
+        done = 0
+        while done < self.iters:
+            k = min(self.stride, self.iters - done)
+            N.ising_iterate(self.h, x, self.alpha, self.beta, k, stream=sid)
+            done += k
+            N.ising_energy(self.h, x, E_int=E, stream=sid)
+            N.ising_synchronize(self.h, sid)
+            traj.append((done, E.cpu().numpy().astype(np.float64)))
+        return sec, traj
+
+    def extra(self, sid, stream):
+        forms = {}
+        for name, x0 in (("bf16_tensor_cores", self.x0_bf16), ("f32_cuda_cores", self.x0_f32)):
+            sec, traj = self._form(x0, sid, stream)
+            Ef = traj[-1][1]
+            forms[name] = {"spin_updates_per_s": self.units / sec, "ms_per_iteration": 1e3 * sec / self.iters,
+                           "E_best": float(Ef.min()), "E_mean": float(Ef.mean()), "E_std": float(Ef.std()),
+                           "mean_E_trace": [[k, float(e.mean())] for k, e in traj], "_traj": traj,
+                           "_sec": sec}
+        target = forms["f32_cuda_cores"]["E_mean"]
+        thresh = target + self.tol * abs(target)       # energies are negative: within tol above the target
+        for f in forms.values():
+            hit = next((k for k, e in f.pop("_traj") if e.mean() <= thresh), None)
+            sec = f.pop("_sec")
+            f["iters_to_equal_energy"] = hit
+            f["s_to_equal_energy"] = None if hit is None else sec * hit / self.iters
+        b, f = forms["bf16_tensor_cores"], forms["f32_cuda_cores"]
+        return {"forms": forms,
+                "equal_energy": {"target_mean_E": target, "tol": self.tol,
+                                 "mean_E_rel_diff": (b["E_mean"] - f["E_mean"]) / abs(f["E_mean"]),
+                                 "best_E_rel_diff": (b["E_best"] - f["E_best"]) / abs(f["E_best"]),
+                                 "speedup_at_equal_energy": (f["s_to_equal_energy"] / b["s_to_equal_energy"])
+                                 if b["s_to_equal_energy"] and f["s_to_equal_energy"] else None,
+                                 "spin_update_rate_ratio": b["spin_updates_per_s"] / f["spin_updates_per_s"]}}
+
+    def roofline(self, per_launch_s):
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
+        flops = 2.0 * self.n * self.n * self.R
+        ach = flops / per_launch_s / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": self.dominant, "peak_kind": "measured (bf16 sustained)",
+                "algorithmic_flops_per_launch": flops}
+
+    def e2e(self, n_steps, sid):
+        return Dense.e2e(self, n_steps, sid)
+
+    def cpu_baseline(self, args):
+        return Dense.cpu_baseline(self, args)
 
     def close(self):
         self.N.ising_destroy(self.h)
@@ -765,9 +880,10 @@ class S5:
 
     def cpu_baseline(self, args):
         import oracle as O
+        from oracle import matrices as M
         from paper_2509_01928_gb300 import inputs as I
         n, p, iters = 20000, 0.1, 200
-        J = I.s5_csr(n, p, seed=17)
+        J = M.s5_csr(n, p, seed=17)
         x0 = I.x0_uniform(n, self.R, seed=18, dtype=np.float64)
         a, b = O.alpha_beta(J, eta=1.0, method="wigner")
         P = O.Problem(J)
@@ -853,9 +969,10 @@ class Proc:
 
     def cpu_baseline(self, args):
         import oracle as O
+        from oracle import matrices as M
         from paper_2509_01928_gb300 import inputs as I
         n, iters = 4000, 300
-        J = I.procedural_sin(n, 100)
+        J = M.procedural_sin(n, 100)
         x0 = I.x0_uniform(n, self.R, seed=SEED, dtype=np.float64)
         a, b = O.alpha_beta(J, eta=1.0, method="wigner")
         P = O.Problem(J)
@@ -871,7 +988,7 @@ class Proc:
 
 
 WORKLOADS = {"torus": Torus, "dense": Dense, "batched": Batched, "backward": Backward, "er800": Er800,
-             "adoch": Adoch, "s5": S5, "proc": Proc}
+             "adoch": Adoch, "s5": S5, "proc": Proc, "precision": Precision}
 
 
 def run_ours(args):
@@ -937,6 +1054,7 @@ def run_ours(args):
     e2e_t, h2d, d2h, how = wl.e2e(n_e2e, sid)
     (e2e_t,) = max_over_ranks([e2e_t])
     e2e_val = job_rate(wl.units, n_e2e, world, e2e_t)
+    extra = wl.extra(sid, stream) if hasattr(wl, "extra") else None
     wl.close()
 
     if rank != 0:
@@ -961,6 +1079,8 @@ def run_ours(args):
         "clocks": clocks,
         "dominant_ms_per_step": 1e3 * dom_s / args.steps,
     }
+    if extra is not None:
+        line["precision"] = extra
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -982,7 +1102,8 @@ def main():
                     help="torus (default: 10^4 x 10^4 lattice), dense (16384 x 256 on tcgen05), "
                          "batched (512 uneven instances), backward (adjoint, n = 1e5), er800 (FP64), "
                          "adoch (Algorithm 2 on the 10^4 x 10^4 lattice), s5 (Algorithm S5 matrix generated on "
-                         "the device, n = 1e5), proc (procedural dense sin(ij + 100), n = 1e6)")
+                         "the device, n = 1e5), proc (procedural dense sin(ij + 100), n = 1e6), precision (dense 16384 x 256: "
+                         "BF16 tensor-core form against the plain FP32 form at equal final energy)")
     ap.add_argument("--dense-n", type=int, default=16384)
     ap.add_argument("--dense-iters", type=int, default=1000)
     ap.add_argument("--batch-count", type=int, default=512)
@@ -993,6 +1114,8 @@ def main():
     ap.add_argument("--s5-iters", type=int, default=500)
     ap.add_argument("--proc-n", type=int, default=1000000)
     ap.add_argument("--proc-iters", type=int, default=10)
+    ap.add_argument("--precision-stride", type=int, default=50, help="iterations between energy readouts")
+    ap.add_argument("--precision-tol", type=float, default=0.005, help="relative tolerance of equal final energy")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

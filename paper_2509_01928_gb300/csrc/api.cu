@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -458,7 +460,9 @@ void destroy_ctx(ising_context *c) {
     c->params.release();
     c->ckpt.release();
     c->work.release();
-    c->batch_items.release();
+    c->res_items[0].buf.release();
+    c->res_items[1].buf.release();
+    c->res_scratch.release();
     c->proc_units.release();
     c->proc_acc.release();
     c->proc_u.release();
@@ -743,20 +747,128 @@ ising_status_t tune_batched(ising_context *c, const float *x, int R, const Param
     return ISING_OK;
 }
 
+// Autotuner for the shared-memory resident kernel: times each variant (threads
+// per CTA; one or two iterate copies in shared memory) for a few steps on a
+// scratch copy of x and keeps the fastest, per R.
+ising_status_t tune_resident(ising_context *c, const float *x, int R, const ParamTabs &p, cudaStream_t st,
+                             ResidentConfig *out) {
+    auto it = c->res_tuned.find(R);
+    if (it != c->res_tuned.end()) {
+        *out = it->second;
+        return ISING_OK;
+    }
+    // ISING_RESIDENT_VARIANT=<threads>:<copies> (512 or 1024 : 1 or 2) fixes the variant
+    // instead of timing the candidates (to test each variant)
+    if (const char *env = std::getenv("ISING_RESIDENT_VARIANT")) {
+        int t = 0, cp = 0;
+        if (std::sscanf(env, "%d:%d", &t, &cp) == 2 && (t == 512 || t == 1024) && (cp == 1 || cp == 2)) {
+            ResidentConfig k;
+            k.threads = t;
+            k.one_copy = cp == 1;
+            DOCH_CHECK(resident_items(c, R, k.one_copy));
+            c->res_tuned[R] = k;
+            *out = k;
+            return ISING_OK;
+        }
+    }
+    const size_t xbytes = static_cast<size_t>(c->n) * R * sizeof(float);
+    DOCH_CHECK(c->work.ensure(xbytes));
+    float *tx = c->work.as<float>();
+    cudaEvent_t e0, e1;
+    DOCH_CUDA(cudaEventCreate(&e0));
+    DOCH_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    ResidentConfig best;
+    bool any = false;
+    const int probe = 16;
+    for (int threads : {1024, 512})
+        for (bool one : {false, true}) {
+            ResidentConfig k;
+            k.threads = threads;
+            k.one_copy = one;
+            DOCH_CUDA(cudaMemcpyAsync(tx, x, xbytes, cudaMemcpyDeviceToDevice, st));
+            const ising_status_t ws = batched_resident_launch(c, k, tx, R, p, 2, st);  // warm-up
+            if (ws == ISING_ERR_UNSUPPORTED) continue;
+            DOCH_CHECK(ws);
+            any = true;
+            DOCH_CUDA(cudaEventRecord(e0, st));
+            DOCH_CHECK(batched_resident_launch(c, k, tx, R, p, probe, st));
+            DOCH_CUDA(cudaEventRecord(e1, st));
+            DOCH_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DOCH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = k;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!any) return ISING_ERR_UNSUPPORTED;
+    g_err.clear();
+    c->res_tuned[R] = best;
+    *out = best;
+    return ISING_OK;
+}
+
+// capture `launch` (enqueued on the handle's capture stream) into the handle's
+// graph unless the graph for `key` exists, then replay it on st
+template <typename F>
+ising_status_t graph_replay(ising_context *c, const std::vector<uintptr_t> &key, F &&launch, cudaStream_t st) {
+    if (!c->batch_exec || c->batch_key != key) {
+        if (c->batch_exec) {
+            cudaGraphExecDestroy(c->batch_exec);
+            c->batch_exec = nullptr;
+        }
+        if (!c->cap_stream) DOCH_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        DOCH_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const ising_status_t s = launch(c->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (s != ISING_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        DOCH_CUDA(ee);
+        const cudaError_t ei = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        DOCH_CUDA(ei);
+        c->batch_key = key;
+    }
+    DOCH_CUDA(cudaGraphLaunch(c->batch_exec, st));
+    return ISING_OK;
+}
+
 // All steps of all instances: one persistent launch, captured once into a
 // CUDA graph (queue reset + kernel [+ copy back]) and replayed while the
 // buffers, parameters and shape stay the same.
 ising_status_t batched_iterate(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
                                cudaStream_t st) {
     // every (instance, replica group) resident in shared memory when they fit
-    const ising_status_t rs = batched_resident_launch(c, x, R, p, iters, st);
-    if (rs != ISING_ERR_UNSUPPORTED) return rs;
+    if (batched_resident_ok(c, x, R)) {
+        ResidentConfig rc;
+        DOCH_CHECK(tune_resident(c, x, R, p, st, &rc));
+        DOCH_CHECK(resident_items(c, R, rc.one_copy));   // built here, never inside the capture
+        if (rc.one_copy) DOCH_CHECK(c->res_scratch.ensure(static_cast<size_t>(c->n) * R * sizeof(float)));
+        const ResidentItems &its = c->res_items[rc.one_copy ? 1 : 0];
+        const std::vector<uintptr_t> key = {1, static_cast<uintptr_t>(its.gen), reinterpret_cast<uintptr_t>(x),
+                                            static_cast<uintptr_t>(R),
+                                            static_cast<uintptr_t>(iters), static_cast<uintptr_t>(p.alpha_len),
+                                            reinterpret_cast<uintptr_t>(p.alpha_f),
+                                            reinterpret_cast<uintptr_t>(p.zscale_f),
+                                            reinterpret_cast<uintptr_t>(p.xscale_f),
+                                            static_cast<uintptr_t>(rc.threads), static_cast<uintptr_t>(rc.one_copy),
+                                            reinterpret_cast<uintptr_t>(its.buf.ptr),
+                                            reinterpret_cast<uintptr_t>(c->res_scratch.ptr)};
+        return graph_replay(c, key, [&](cudaStream_t cs) { return batched_resident_launch(c, rc, x, R, p, iters, cs); },
+                            st);
+    }
     BatchedConfig cfg;
     DOCH_CHECK(tune_batched(c, x, R, p, st, &cfg));
     const size_t xbytes = static_cast<size_t>(c->n) * R * sizeof(float);
     DOCH_CHECK(c->ping.ensure(xbytes));
     float *xb = c->ping.as<float>();
-    const std::vector<uintptr_t> key = {reinterpret_cast<uintptr_t>(x), reinterpret_cast<uintptr_t>(xb),
+    const std::vector<uintptr_t> key = {2, reinterpret_cast<uintptr_t>(x), reinterpret_cast<uintptr_t>(xb),
                                         static_cast<uintptr_t>(R), static_cast<uintptr_t>(iters),
                                         static_cast<uintptr_t>(p.alpha_len), reinterpret_cast<uintptr_t>(p.alpha_f),
                                         reinterpret_cast<uintptr_t>(p.inv_beta_f), static_cast<uintptr_t>(cfg.threads),
@@ -1256,8 +1368,13 @@ ising_status_t ising_iterate_until(ising_handle_t h, void *x, int32_t xtype, int
         // ends each (instance, replica group) as soon as all of its replicas stopped
         ising_status_t rs = ISING_ERR_UNSUPPORTED;
         if (c->format == ISING_FMT_CSR && c->n_inst > 1 && xtype == ISING_F32 && max_iters > 0)
-            rs = batched_resident_launch(c, static_cast<float *>(xd), R, p, max_iters, st, static_cast<float>(eps),
-                                         s.steps);
+            if (batched_resident_ok(c, static_cast<float *>(xd), R)) {
+            ResidentConfig rc;
+            rs = tune_resident(c, static_cast<float *>(xd), R, p, st, &rc);
+            if (rs == ISING_OK)
+                rs = batched_resident_launch(c, rc, static_cast<float *>(xd), R, p, max_iters, st,
+                                             static_cast<float>(eps), s.steps);
+        }
         if (rs != ISING_OK && rs != ISING_ERR_UNSUPPORTED) return rs;
         if (rs == ISING_ERR_UNSUPPORTED) {
             if (!c->count_host) DOCH_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&c->count_host), sizeof(int), 0));
@@ -1506,7 +1623,7 @@ ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, i
                 DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
         // loss and g^N (x^N is the last iterate of the last segment)
         int gc = 0;
-        DOCH_CHECK(csr_loss_grad(c, xs(S - 1, seg_len(S - 1)), xtype, gbuf[gc], R, V, grid, lpart, st));
+        DOCH_CHECK(csr_loss_w(c, xs(S - 1, seg_len(S - 1)), xtype, gbuf[gc], R, V, grid, lpart, zeros_d, st));
         const float inv_beta = static_cast<float>(1.0 / beta);
         for (int sg_i = S - 1; sg_i >= 0; --sg_i) {
             const int len = seg_len(sg_i);
@@ -1515,8 +1632,8 @@ ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, i
                     DOCH_CHECK(csr_step(c, xs(sg_i, m - 1), xs(sg_i, m), xtype, R, p, sg_i * C + m - 1, st));
             for (int m = len - 1; m >= 0; --m) {
                 const int k = sg_i * C + m;
-                DOCH_CHECK(csr_adjoint_step(c, gbuf[gc], xs(sg_i, m + 1), xs(sg_i, m), xtype, gbuf[1 - gc], R, V,
-                                            static_cast<float>(alpha_h[k]), inv_beta, grid,
+                DOCH_CHECK(csr_adjoint_step(c, gbuf[gc], xs(sg_i, m), xtype, gbuf[1 - gc], R, V,
+                                            static_cast<float>(alpha_h[k]), inv_beta, k == 0, grid,
                                             part + static_cast<size_t>(k) * grid, zeros_d, st));
                 gc = 1 - gc;
             }

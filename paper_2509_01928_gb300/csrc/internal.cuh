@@ -71,6 +71,25 @@ struct BatchedConfig {
     int ctas_per_sm = 2;
 };
 
+// variant of the shared-memory resident batched kernel (picked by the autotuner):
+// threads per CTA, and whether both Jacobi copies of an item's iterate sit in
+// shared memory or only x^(k) (the new iterate then goes through global scratch,
+// and items hold twice as many replicas)
+struct ResidentConfig {
+    int threads = 1024;
+    bool one_copy = false;
+};
+
+// work items of the resident kernel for one variant: (instance, first replica, G,
+// ELL slots) as int4, built for R replicas; smem = the largest item's bytes
+struct ResidentItems {
+    DevBuf buf;
+    int gen = 0;  // rebuild counter (part of the key of a captured launch)
+    int R = 0;
+    int count = 0;
+    size_t smem = 0;
+};
+
 // Bounded-wait self-test (k_selftest.cu): one mbarrier wait of limit_ns that
 // nobody satisfies (arrive = false) or that is satisfied at once.
 ising_status_t selftest_wait_launch(int *err, bool arrive, uint64_t limit_ns, cudaStream_t st);
@@ -155,10 +174,9 @@ struct ising_context {
     float *ell_val = nullptr;
     int64_t *ell_off = nullptr;
     std::vector<int> ell_deg_h;
-    doch::DevBuf batch_items;
-    int batch_items_R = 0;
-    int batch_items_count = 0;
-    size_t batch_items_smem = 0;
+    doch::ResidentItems res_items[2];                   // [two copies, one copy]
+    doch::DevBuf res_scratch;                           // one-copy variant: x^(k+1) of every item
+    std::map<int, doch::ResidentConfig> res_tuned;      // by R
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<uintptr_t> batch_key;
@@ -258,8 +276,13 @@ ising_status_t stop_finish(ising_context *c, const void *xc, void *res, int xtyp
 // does not fit or x is not 16-byte aligned. Updates x in place. eps > 0
 // applies the stopping rule of Remark S2 per (instance, replica) inside the
 // kernel (steps: [pair] steps taken, may be NULL).
-ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
-                                       cudaStream_t st, float eps = 0.f, int32_t *steps = nullptr);
+ising_status_t batched_resident_launch(ising_context *c, const ResidentConfig &cfg, float *x, int R,
+                                       const ParamTabs &p, int iters, cudaStream_t st, float eps = 0.f,
+                                       int32_t *steps = nullptr);
+// every instance fits the resident kernel (two-copy variant) and x is 16-byte aligned
+bool batched_resident_ok(ising_context *c, float *x, int R);
+// build (or keep) the resident kernel's work items of a variant for R replicas
+ising_status_t resident_items(ising_context *c, int R, bool one_copy);
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,
                               const ParamTabs &p, int iters, cudaStream_t st);
 
@@ -288,14 +311,15 @@ ising_status_t proc_hamiltonian(ising_context *c, const float *x, int R, const P
 void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2);
 
 // Adjoint (k_backward.cu): CSR couplings, one instance; iterates F32 or F64
-// (xtype), adjoint state g in FP32. g = -(J x + h)/R with per-block loss
-// partials; one adjoint step; FP32 -> FP64 widening; the fixed-order finish.
-ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
-                             int grid, double *part, cudaStream_t st);
-ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
-                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
-                                float inv_beta, int grid, double *part, unsigned long long *zeros,
-                                cudaStream_t st);
+// (xtype), adjoint quantities in FP32. csr_loss_w: g^N = -(J x^N + h)/R with
+// per-block loss partials, stored as w^(N-1) = g^N / (3 (x^N)^2); one adjoint
+// step from w^k and x^k to w^(k-1) (or g^0 when final_step); FP32 -> FP64
+// widening; the fixed-order finish. zeros counts components x^(k) = 0, k >= 1.
+ising_status_t csr_loss_w(const ising_context *c, const void *x, int xtype, float *w, int R, int V, int grid,
+                          double *part, unsigned long long *zeros, cudaStream_t st);
+ising_status_t csr_adjoint_step(const ising_context *c, const float *w_in, const void *x_cur, int xtype,
+                                float *w_out, int R, int V, float alpha_k, float inv_beta, bool final_step,
+                                int grid, double *part, unsigned long long *zeros, cudaStream_t st);
 ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st);
 ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
                                      const double *lpart, int lblocks, int R, double *grad_alpha,

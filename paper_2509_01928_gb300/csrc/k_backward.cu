@@ -20,8 +20,9 @@
 // Memory: x is kept only every C steps (checkpoints); each segment is
 // recomputed from its checkpoint with the forward kernel (deterministic, so
 // the recomputed iterates equal the forward ones) before its adjoint steps
-// run. One adjoint kernel per step forms w_j for every neighbour j on the fly
-// from g^(k+1) and x^(k+1), so w is never stored. dL/dalpha_k and the loss
+// run. The adjoint kernel of step k gathers w^k at the neighbours and forms, for
+// its own rows, g^k and the next step's w^(k-1) = g^k / (3 (x^k)^2): one
+// gather per neighbour; the loss kernel forms w^(N-1) from g^N. dL/dalpha_k and the loss
 // are FP64 per-block partials summed in block order (run-to-run identical).
 //
 // Thread layout as in the forward CSR kernel: one thread per (row, chunk of
@@ -90,16 +91,19 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;
 }
 
-// g = -(J x + h) / R (FP32) and per-block partial sums of -1/2 x u - h x (FP64);
-// the product u is formed in the iterate type XT
+// g^N = -(J x^N + h) / R and per-block partial sums of -1/2 x u - h x (FP64); the
+// kernel stores w^(N-1) = g^N / (3 (x^N)^2) (0 where x^N = 0, counted), the
+// quantity the first adjoint step gathers. The product u is formed in the
+// iterate type XT.
 template <typename XT, typename VT, int V>
 __global__ void __launch_bounds__(kBThreads)
-loss_grad_kernel(const XT *__restrict__ x, float *__restrict__ g, const int64_t *__restrict__ row_ptr,
-                 const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
-                 int64_t n, int R, double *__restrict__ part) {
+loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__restrict__ row_ptr,
+              const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
+              int64_t n, int R, double *__restrict__ part, unsigned long long *__restrict__ zeros) {
     const int C = R / V;
     const XT invR = XT(1) / static_cast<XT>(R);
     double acc = 0.0;
+    unsigned nz = 0;
     const int rows_per_block = kBThreads / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
@@ -110,36 +114,44 @@ loss_grad_kernel(const XT *__restrict__ x, float *__restrict__ g, const int64_t 
         for (int q = 0; q < V; ++q) u[q] = XT(0);
         const int64_t e1 = __ldg(row_ptr + i + 1);
         for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
-            const XT w = static_cast<XT>(__ldg(val + e));
+            const XT wv = static_cast<XT>(__ldg(val + e));
             XT xv[V];
             ld<V>(x + static_cast<int64_t>(__ldg(col + e)) * R + ch * V, xv);
 #pragma unroll
-            for (int q = 0; q < V; ++q) u[q] += w * xv[q];
+            for (int q = 0; q < V; ++q) u[q] += wv * xv[q];
         }
         XT xi[V];
-        float gi[V];
+        float wi[V];
         ld<V>(x + i * R + ch * V, xi);
         const XT hi = h ? h[i] : XT(0);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             acc += -0.5 * static_cast<double>(xi[q]) * static_cast<double>(u[q]) -
                    static_cast<double>(hi) * static_cast<double>(xi[q]);
-            gi[q] = static_cast<float>(-(u[q] + hi) * invR);
+            const float gi = static_cast<float>(-(u[q] + hi) * invR);
+            nz += xi[q] == XT(0);
+            wi[q] = dcbrt_weight(gi, static_cast<float>(xi[q]));
         }
-        st<V>(g + i * R + ch * V, gi);
+        st<V>(w + i * R + ch * V, wi);
     }
     const double b = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
+    unsigned tot = nz;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(zeros, static_cast<unsigned long long>(tot));
 }
 
-// one adjoint step: g_out = (J w + alpha_k w) / beta, w = g_in / (3 x_next^2);
-// iterates of type XT are rounded to FP32 for the adjoint arithmetic
+// One adjoint step k: from w^k (gathered at the neighbours) and x^k (the row's own),
+//   dL/dalpha_k partial += w^k_i x^k_i,  g^k_i = (sum_j J_ij w^k_j + alpha_k w^k_i) / beta,
+// then the next step's w^(k-1)_i = g^k_i / (3 (x^k_i)^2) (0 where x^k_i = 0, counted),
+// or g^0 itself when k = 0 (final). One gather per neighbour: w^k was formed once per
+// row by the step before. Iterates of type XT are rounded to FP32 for this arithmetic.
 template <typename XT, typename VT, int V>
 __global__ void __launch_bounds__(kBThreads)
-adjoint_step_kernel(const float *__restrict__ g_in, const XT *__restrict__ x_next,
-                    const XT *__restrict__ x_cur, float *__restrict__ g_out,
+adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur, float *__restrict__ w_out,
                     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                    const VT *__restrict__ val, int64_t n, int R, float alpha_k, float inv_beta,
+                    const VT *__restrict__ val, int64_t n, int R, float alpha_k, float inv_beta, int final_step,
                     double *__restrict__ part, unsigned long long *__restrict__ zeros) {
     const int C = R / V;
     double ga = 0.0;
@@ -155,27 +167,28 @@ adjoint_step_kernel(const float *__restrict__ g_in, const XT *__restrict__ x_nex
         const int64_t e1 = __ldg(row_ptr + i + 1);
         for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
             const int64_t j = __ldg(col + e);
-            const float w = static_cast<float>(__ldg(val + e));
-            float gj[V];
-            XT xj[V];
-            ld<V>(g_in + j * R + ch * V, gj);
-            ld<V>(x_next + j * R + ch * V, xj);
+            const float wv = static_cast<float>(__ldg(val + e));
+            float wj[V];
+            ld<V>(w_in + j * R + ch * V, wj);
 #pragma unroll
-            for (int q = 0; q < V; ++q) acc[q] += w * dcbrt_weight(gj[q], static_cast<float>(xj[q]));
+            for (int q = 0; q < V; ++q) acc[q] += wv * wj[q];
         }
-        float gi[V], out[V];
-        XT xn[V], xc[V];
-        ld<V>(g_in + i * R + ch * V, gi);
-        ld<V>(x_next + i * R + ch * V, xn);
+        float wi[V], out[V];
+        XT xc[V];
+        ld<V>(w_in + i * R + ch * V, wi);
         ld<V>(x_cur + i * R + ch * V, xc);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            const float wi = dcbrt_weight(gi[q], static_cast<float>(xn[q]));
-            nz += xn[q] == XT(0);
-            ga += static_cast<double>(wi) * static_cast<double>(xc[q]);
-            out[q] = (acc[q] + alpha_k * wi) * inv_beta;
+            ga += static_cast<double>(wi[q]) * static_cast<double>(xc[q]);
+            const float g = (acc[q] + alpha_k * wi[q]) * inv_beta;
+            if (final_step) {
+                out[q] = g;
+            } else {
+                nz += xc[q] == XT(0);
+                out[q] = dcbrt_weight(g, static_cast<float>(xc[q]));
+            }
         }
-        st<V>(g_out + i * R + ch * V, out);
+        st<V>(w_out + i * R + ch * V, out);
     }
     const double b = block_sum(ga);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
@@ -209,87 +222,83 @@ __global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b
 }
 
 template <typename XT, typename VT, int V>
-void launch_loss(const ising_context *c, const XT *x, float *g, int R, int grid, double *part,
-                 cudaStream_t st) {
+void launch_loss(const ising_context *c, const XT *x, float *w, int R, int grid, double *part,
+                 unsigned long long *zeros, cudaStream_t st) {
     const XT *h = nullptr;
     if constexpr (sizeof(XT) == 8) h = c->h_f64; else h = c->h_f32;
-    loss_grad_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(x, g, c->row_ptr, c->col,
-                                                            static_cast<const VT *>(c->val), h, c->n,
-                                                            R, part);
+    loss_w_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(x, w, c->row_ptr, c->col, static_cast<const VT *>(c->val),
+                                                         h, c->n, R, part, zeros);
 }
 
 template <typename XT, typename VT, int V>
-void launch_adj(const ising_context *c, const float *gi, const XT *xn, const XT *xc, float *go,
-                int R, float a, float ib, int grid, double *part, unsigned long long *zeros,
-                cudaStream_t st) {
-    adjoint_step_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(gi, xn, xc, go, c->row_ptr, c->col,
-                                                               static_cast<const VT *>(c->val), c->n, R,
-                                                               a, ib, part, zeros);
+void launch_adj(const ising_context *c, const float *wi, const XT *xc, float *wo, int R, float a, float ib,
+                int final_step, int grid, double *part, unsigned long long *zeros, cudaStream_t st) {
+    adjoint_step_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(wi, xc, wo, c->row_ptr, c->col,
+                                                               static_cast<const VT *>(c->val), c->n, R, a, ib,
+                                                               final_step, part, zeros);
 }
 
 template <typename XT, typename VT>
-ising_status_t loss_v(const ising_context *c, const XT *x, float *g, int R, int V, int grid,
-                      double *part, cudaStream_t st) {
-    if (V == 4) launch_loss<XT, VT, 4>(c, x, g, R, grid, part, st);
-    else if (V == 2) launch_loss<XT, VT, 2>(c, x, g, R, grid, part, st);
-    else launch_loss<XT, VT, 1>(c, x, g, R, grid, part, st);
+ising_status_t loss_v(const ising_context *c, const XT *x, float *w, int R, int V, int grid, double *part,
+                      unsigned long long *zeros, cudaStream_t st) {
+    if (V == 4) launch_loss<XT, VT, 4>(c, x, w, R, grid, part, zeros, st);
+    else if (V == 2) launch_loss<XT, VT, 2>(c, x, w, R, grid, part, zeros, st);
+    else launch_loss<XT, VT, 1>(c, x, w, R, grid, part, zeros, st);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
 
 template <typename XT, typename VT>
-ising_status_t adj_v(const ising_context *c, const float *gi, const XT *xn, const XT *xc,
-                     float *go, int R, int V, float a, float ib, int grid, double *part,
-                     unsigned long long *zeros, cudaStream_t st) {
-    if (V == 4) launch_adj<XT, VT, 4>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
-    else if (V == 2) launch_adj<XT, VT, 2>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
-    else launch_adj<XT, VT, 1>(c, gi, xn, xc, go, R, a, ib, grid, part, zeros, st);
+ising_status_t adj_v(const ising_context *c, const float *wi, const XT *xc, float *wo, int R, int V, float a,
+                     float ib, int final_step, int grid, double *part, unsigned long long *zeros, cudaStream_t st) {
+    if (V == 4) launch_adj<XT, VT, 4>(c, wi, xc, wo, R, a, ib, final_step, grid, part, zeros, st);
+    else if (V == 2) launch_adj<XT, VT, 2>(c, wi, xc, wo, R, a, ib, final_step, grid, part, zeros, st);
+    else launch_adj<XT, VT, 1>(c, wi, xc, wo, R, a, ib, final_step, grid, part, zeros, st);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
 
 template <typename XT>
-ising_status_t loss_t(const ising_context *c, const XT *x, float *g, int R, int V, int grid,
-                      double *part, cudaStream_t st) {
+ising_status_t loss_t(const ising_context *c, const XT *x, float *w, int R, int V, int grid, double *part,
+                      unsigned long long *zeros, cudaStream_t st) {
     switch (c->jtype) {
-        case ISING_I8: return loss_v<XT, int8_t>(c, x, g, R, V, grid, part, st);
-        case ISING_I32: return loss_v<XT, int32_t>(c, x, g, R, V, grid, part, st);
-        case ISING_F32: return loss_v<XT, float>(c, x, g, R, V, grid, part, st);
-        case ISING_F64: return loss_v<XT, double>(c, x, g, R, V, grid, part, st);
+        case ISING_I8: return loss_v<XT, int8_t>(c, x, w, R, V, grid, part, zeros, st);
+        case ISING_I32: return loss_v<XT, int32_t>(c, x, w, R, V, grid, part, zeros, st);
+        case ISING_F32: return loss_v<XT, float>(c, x, w, R, V, grid, part, zeros, st);
+        case ISING_F64: return loss_v<XT, double>(c, x, w, R, V, grid, part, zeros, st);
         default: return fail(ISING_ERR_UNSUPPORTED, "backward: coupling type");
     }
 }
 
 template <typename XT>
-ising_status_t adj_t(const ising_context *c, const float *g_in, const XT *x_next, const XT *x_cur,
-                     float *g_out, int R, int V, float alpha_k, float inv_beta, int grid, double *part,
+ising_status_t adj_t(const ising_context *c, const float *wi, const XT *xc, float *wo, int R, int V,
+                     float alpha_k, float inv_beta, int final_step, int grid, double *part,
                      unsigned long long *zeros, cudaStream_t st) {
     switch (c->jtype) {
-        case ISING_I8: return adj_v<XT, int8_t>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
-        case ISING_I32: return adj_v<XT, int32_t>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
-        case ISING_F32: return adj_v<XT, float>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
-        case ISING_F64: return adj_v<XT, double>(c, g_in, x_next, x_cur, g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        case ISING_I8: return adj_v<XT, int8_t>(c, wi, xc, wo, R, V, alpha_k, inv_beta, final_step, grid, part, zeros, st);
+        case ISING_I32: return adj_v<XT, int32_t>(c, wi, xc, wo, R, V, alpha_k, inv_beta, final_step, grid, part, zeros, st);
+        case ISING_F32: return adj_v<XT, float>(c, wi, xc, wo, R, V, alpha_k, inv_beta, final_step, grid, part, zeros, st);
+        case ISING_F64: return adj_v<XT, double>(c, wi, xc, wo, R, V, alpha_k, inv_beta, final_step, grid, part, zeros, st);
         default: return fail(ISING_ERR_UNSUPPORTED, "backward: coupling type");
     }
 }
 
 }  // namespace
 
-ising_status_t csr_loss_grad(const ising_context *c, const void *x, int xtype, float *g, int R, int V,
-                             int grid, double *part, cudaStream_t st) {
-    if (xtype == ISING_F64) return loss_t<double>(c, static_cast<const double *>(x), g, R, V, grid, part, st);
-    return loss_t<float>(c, static_cast<const float *>(x), g, R, V, grid, part, st);
+ising_status_t csr_loss_w(const ising_context *c, const void *x, int xtype, float *w, int R, int V, int grid,
+                          double *part, unsigned long long *zeros, cudaStream_t st) {
+    if (xtype == ISING_F64) return loss_t<double>(c, static_cast<const double *>(x), w, R, V, grid, part, zeros, st);
+    return loss_t<float>(c, static_cast<const float *>(x), w, R, V, grid, part, zeros, st);
 }
 
-ising_status_t csr_adjoint_step(const ising_context *c, const float *g_in, const void *x_next,
-                                const void *x_cur, int xtype, float *g_out, int R, int V, float alpha_k,
-                                float inv_beta, int grid, double *part, unsigned long long *zeros,
-                                cudaStream_t st) {
+ising_status_t csr_adjoint_step(const ising_context *c, const float *w_in, const void *x_cur, int xtype,
+                                float *w_out, int R, int V, float alpha_k, float inv_beta, bool final_step,
+                                int grid, double *part, unsigned long long *zeros, cudaStream_t st) {
     if (xtype == ISING_F64)
-        return adj_t<double>(c, g_in, static_cast<const double *>(x_next), static_cast<const double *>(x_cur),
-                             g_out, R, V, alpha_k, inv_beta, grid, part, zeros, st);
-    return adj_t<float>(c, g_in, static_cast<const float *>(x_next), static_cast<const float *>(x_cur), g_out,
-                        R, V, alpha_k, inv_beta, grid, part, zeros, st);
+        return adj_t<double>(c, w_in, static_cast<const double *>(x_cur), w_out, R, V, alpha_k, inv_beta,
+                             final_step ? 1 : 0, grid, part, zeros, st);
+    return adj_t<float>(c, w_in, static_cast<const float *>(x_cur), w_out, R, V, alpha_k, inv_beta,
+                        final_step ? 1 : 0, grid, part, zeros, st);
 }
 
 ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int num_sms, cudaStream_t st) {

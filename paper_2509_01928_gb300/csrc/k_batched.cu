@@ -205,12 +205,16 @@ struct ResidentStop {
     int *all_frozen;
 };
 
-template <int G, bool STOP>
+// ONECOPY: only x^(k) is held in shared memory ([n_b][G] floats, so G can be
+// twice as large as with two copies); each step writes x^(k+1) to the item's
+// own contiguous region `gx` of a global scratch array ([n_b][G] floats, L2
+// resident) and, after a barrier, reads it back into shared memory.
+template <int G, bool STOP, bool ONECOPY>
 __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int64_t lo, int nb, int g0, int D,
                                               const uint16_t *__restrict__ ecol, const float *__restrict__ eval,
                                               const float *__restrict__ h, const float *__restrict__ alpha_row,
                                               int alpha_len, float zs, float xsc, int iters, float *s0, float *s1,
-                                              int pair0, const ResidentStop &stop) {
+                                              float *gx, int pair0, const ResidentStop &stop) {
     const int T = blockDim.x;
     constexpr bool stopping = STOP;
     for (int i = threadIdx.x; i < nb; i += T) {
@@ -275,7 +279,8 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
                     ssum[q] += xs[q] * xs[q];
                 }
             }
-            st_vec<G>(nxt + i * G, out);
+            if constexpr (ONECOPY) st_vec<G>(gx + static_cast<int64_t>(i) * G, out);
+            else st_vec<G>(nxt + i * G, out);
         }
         if constexpr (STOP) {
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,23 +317,41 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
             }
         }
         __syncthreads();
-        float *t = cur; cur = nxt; nxt = t;
+        if constexpr (ONECOPY) {
+            // x^(k+1) back into shared memory (the global writes of this block are visible
+            // after the barrier; plain loads, as the data was written in this launch)
+            if (k + 1 < iters && !(STOP && *stop.all_frozen)) {
+                for (int i = threadIdx.x; i < nb; i += T) {
+                    float v[G];
+                    ldg_vec<G>(gx + static_cast<int64_t>(i) * G, v);
+                    st_vec<G>(cur + i * G, v);
+                }
+                __syncthreads();
+            }
+        } else {
+            float *t = cur; cur = nxt; nxt = t;
+        }
         if (STOP && *stop.all_frozen) break;  // uniform: read after the barrier
     }
     for (int i = threadIdx.x; i < nb; i += T) {
         float v[G];
-        ldg_vec<G>(cur + i * G, v);
+        if constexpr (ONECOPY) {
+            if (iters > 0) ldg_vec<G>(gx + static_cast<int64_t>(i) * G, v);
+            else ldg_vec<G>(cur + i * G, v);
+        } else {
+            ldg_vec<G>(cur + i * G, v);
+        }
         st_vec<G>(x + (lo + i) * R + g0, v);
     }
 }
 
-template <bool STOP>
-__global__ void __launch_bounds__(1024, 1)
+template <bool STOP, bool ONECOPY, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 batched_resident(float *__restrict__ x, const uint16_t *__restrict__ ell_col, const float *__restrict__ ell_val,
                  const int64_t *__restrict__ ell_off, const float *__restrict__ h, const int64_t *__restrict__ off,
                  const int4 *__restrict__ items, int n_items, int R, const float *__restrict__ alpha_tab,
                  int alpha_len, const float *__restrict__ zscale_tab, const float *__restrict__ xscale_tab,
-                 int iters, float eps, int32_t *__restrict__ steps, int *__restrict__ queue) {
+                 int iters, float eps, int32_t *__restrict__ steps, int *__restrict__ queue, float *scratch) {
     extern __shared__ float4 res_smem4[];
     __shared__ int next;
     __shared__ float stop_red[STOP ? 32 : 1][32];
@@ -346,82 +369,118 @@ batched_resident(float *__restrict__ x, const uint16_t *__restrict__ ell_col, co
         const int64_t lo = __ldg(off + b);
         const int nb = static_cast<int>(__ldg(off + b + 1) - lo);
         float *s0 = reinterpret_cast<float *>(res_smem4);
-        float *s1 = s0 + static_cast<size_t>(nb) * it.z;
+        float *s1 = ONECOPY ? s0 : s0 + static_cast<size_t>(nb) * it.z;
+        // the item's region of the one-copy scratch: [instance][replica group][n_b][G]
+        float *gx = ONECOPY ? scratch + lo * R + static_cast<int64_t>(it.y) * nb : nullptr;
         const float *arow = alpha_tab + static_cast<int64_t>(b) * alpha_len;
         const float zs = __ldg(zscale_tab + b), xsc = __ldg(xscale_tab + b);
         const int64_t eo = __ldg(ell_off + b);
         const uint16_t *ec = ell_col + eo;
         const float *ev = ell_val + eo;
         switch (it.z) {
-            case 16: resident_item<16, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
-            case 8: resident_item<8, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
-            case 4: resident_item<4, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
-            case 2: resident_item<2, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
-            default: resident_item<1, STOP>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, b * R + it.y, stop); break;
+            case 16: resident_item<16, STOP, ONECOPY>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, gx, b * R + it.y, stop); break;
+            case 8: resident_item<8, STOP, ONECOPY>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, gx, b * R + it.y, stop); break;
+            case 4: resident_item<4, STOP, ONECOPY>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, gx, b * R + it.y, stop); break;
+            case 2: resident_item<2, STOP, ONECOPY>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, gx, b * R + it.y, stop); break;
+            default: resident_item<1, STOP, ONECOPY>(x, R, lo, nb, it.y, it.w, ec, ev, h, arow, alpha_len, zs, xsc, iters, s0, s1, gx, b * R + it.y, stop); break;
         }
     }
 }
 
-ising_status_t launch_resident(ising_context *c, float *x, int R, const ParamTabs &p, int iters, float eps,
-                               int32_t *steps, cudaStream_t st) {
-    auto kern = eps > 0.f ? batched_resident<true> : batched_resident<false>;
-    const int smem = static_cast<int>(c->batch_items_smem);
+template <bool STOP, bool ONECOPY, int THREADS>
+ising_status_t launch_resident_t(ising_context *c, const ResidentItems &its, float *x, int R, const ParamTabs &p,
+                                 int iters, float eps, int32_t *steps, float *scratch, cudaStream_t st) {
+    auto kern = batched_resident<STOP, ONECOPY, THREADS>;
+    const int smem = static_cast<int>(its.smem);
     DOCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
-    DOCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 1024, smem));
+    DOCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem));
     if (occ < 1) return ISING_ERR_UNSUPPORTED;
     int grid = c->num_sms * occ;
-    if (grid > c->batch_items_count) grid = c->batch_items_count;
+    if (grid > its.count) grid = its.count;
     DOCH_CUDA(cudaMemsetAsync(c->batch_queue, 0, sizeof(int), st));
-    kern<<<grid, 1024, smem, st>>>(x, c->ell_col, c->ell_val, c->ell_off, c->h_f32, c->inst_off,
-                                   c->batch_items.as<int4>(), c->batch_items_count, R, p.alpha_f, p.alpha_len,
-                                   p.zscale_f, p.xscale_f, iters, eps, steps, c->batch_queue);
+    kern<<<grid, THREADS, smem, st>>>(x, c->ell_col, c->ell_val, c->ell_off, c->h_f32, c->inst_off,
+                                      its.buf.as<int4>(), its.count, R, p.alpha_f, p.alpha_len, p.zscale_f,
+                                      p.xscale_f, iters, eps, steps, c->batch_queue, scratch);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
 
+ising_status_t launch_resident(ising_context *c, const ResidentConfig &cfg, float *x, int R, const ParamTabs &p,
+                               int iters, float eps, int32_t *steps, float *scratch, cudaStream_t st) {
+    const ResidentItems &its = c->res_items[cfg.one_copy ? 1 : 0];
+    const bool stop = eps > 0.f;
+#define DOCH_RES_LAUNCH(S, O, T) return launch_resident_t<S, O, T>(c, its, x, R, p, iters, eps, steps, scratch, st)
+    if (cfg.threads == 512) {
+        if (stop) { if (cfg.one_copy) DOCH_RES_LAUNCH(true, true, 512); DOCH_RES_LAUNCH(true, false, 512); }
+        if (cfg.one_copy) DOCH_RES_LAUNCH(false, true, 512);
+        DOCH_RES_LAUNCH(false, false, 512);
+    }
+    if (stop) { if (cfg.one_copy) DOCH_RES_LAUNCH(true, true, 1024); DOCH_RES_LAUNCH(true, false, 1024); }
+    if (cfg.one_copy) DOCH_RES_LAUNCH(false, true, 1024);
+    DOCH_RES_LAUNCH(false, false, 1024);
+#undef DOCH_RES_LAUNCH
+}
+
 }  // namespace
 
-// Work items of the resident kernel for R replicas (cached per handle and R);
+// Work items of the resident kernel for R replicas (cached per handle, variant and R);
 // ISING_ERR_UNSUPPORTED when an instance does not fit shared memory even with G = 1.
-static ising_status_t resident_items(ising_context *c, int R) {
-    if (c->batch_items_R == R) return ISING_OK;
+// copies = 2 (both Jacobi copies in shared memory) or 1 (one copy, the new iterate
+// through the global scratch).
+ising_status_t resident_items(ising_context *c, int R, bool one_copy) {
+    ResidentItems &its = c->res_items[one_copy ? 1 : 0];
+    if (its.R == R) return its.count > 0 ? ISING_OK : ISING_ERR_UNSUPPORTED;
+    ++its.gen;
     int dev = 0, optin = 0;
     DOCH_CUDA(cudaGetDevice(&dev));
     DOCH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int64_t cap = optin - 5120;  // the kernel's static shared memory (queue slot, stopping-rule sums)
+    const int64_t copies = one_copy ? 1 : 2;
     struct Item { int64_t work; int b, g0, G; };
     std::vector<Item> items;
     size_t smem = 0;
+    its.R = R;
+    its.count = 0;
     for (int b = 0; b < c->n_inst; ++b) {
         const int64_t nb = c->inst_off_h[b + 1] - c->inst_off_h[b];
         int G = 16;
-        while (G > 1 && (R % G != 0 || 2 * nb * G * 4 > cap)) G >>= 1;
-        if (2 * nb * G * 4 > cap) return ISING_ERR_UNSUPPORTED;
+        while (G > 1 && (R % G != 0 || copies * nb * G * 4 > cap)) G >>= 1;
+        if (copies * nb * G * 4 > cap) return ISING_ERR_UNSUPPORTED;
         if (static_cast<int64_t>(c->ell_deg_h[b]) * nb >= (int64_t(1) << 31)) return ISING_ERR_UNSUPPORTED;
-        smem = std::max(smem, static_cast<size_t>(2 * nb * G * 4));
+        smem = std::max(smem, static_cast<size_t>(copies * nb * G * 4));
         for (int g0 = 0; g0 < R; g0 += G) items.push_back({(nb + c->inst_nnz_h[b]) * G, b, g0, G});
     }
     std::stable_sort(items.begin(), items.end(), [](const Item &u, const Item &v) { return u.work > v.work; });
     std::vector<int4> host(items.size());
     for (size_t i = 0; i < items.size(); ++i)
         host[i] = make_int4(items[i].b, items[i].g0, items[i].G, c->ell_deg_h[items[i].b]);
-    DOCH_CHECK(c->batch_items.ensure(sizeof(int4) * host.size()));
-    DOCH_CUDA(cudaMemcpy(c->batch_items.ptr, host.data(), sizeof(int4) * host.size(), cudaMemcpyHostToDevice));
-    c->batch_items_count = static_cast<int>(host.size());
-    c->batch_items_smem = std::max<size_t>(smem, 16);
-    c->batch_items_R = R;
+    DOCH_CHECK(its.buf.ensure(sizeof(int4) * host.size()));
+    DOCH_CUDA(cudaMemcpy(its.buf.ptr, host.data(), sizeof(int4) * host.size(), cudaMemcpyHostToDevice));
+    its.count = static_cast<int>(host.size());
+    its.smem = std::max<size_t>(smem, 16);
     return ISING_OK;
 }
 
-ising_status_t batched_resident_launch(ising_context *c, float *x, int R, const ParamTabs &p, int iters,
-                                       cudaStream_t st, float eps, int32_t *steps) {
+bool batched_resident_ok(ising_context *c, float *x, int R) {
+    if (!c->batch_queue || !c->ell_col || c->inst_nnz_h.size() != static_cast<size_t>(c->n_inst)) return false;
+    if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return false;
+    return resident_items(c, R, false) == ISING_OK;
+}
+
+ising_status_t batched_resident_launch(ising_context *c, const ResidentConfig &cfg, float *x, int R,
+                                       const ParamTabs &p, int iters, cudaStream_t st, float eps, int32_t *steps) {
     if (!c->batch_queue || !c->ell_col || c->inst_nnz_h.size() != static_cast<size_t>(c->n_inst))
         return ISING_ERR_UNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return ISING_ERR_UNSUPPORTED;
-    const ising_status_t s = resident_items(c, R);
+    const ising_status_t s = resident_items(c, R, cfg.one_copy);
     if (s != ISING_OK) return s;
-    return launch_resident(c, x, R, p, iters, eps, steps, st);
+    float *scratch = nullptr;
+    if (cfg.one_copy) {
+        DOCH_CHECK(c->res_scratch.ensure(static_cast<size_t>(c->n) * R * sizeof(float)));
+        scratch = c->res_scratch.as<float>();
+    }
+    return launch_resident(c, cfg, x, R, p, iters, eps, steps, scratch, st);
 }
 
 ising_status_t batched_launch(const ising_context *c, const BatchedConfig &cfg, float *xa, float *xb, int R,

@@ -24,6 +24,7 @@ import oracle as O
 from paper_2509_01928_gb300 import _native as N
 from paper_2509_01928_gb300 import build as B
 from paper_2509_01928_gb300 import inputs as I
+from fp32_bounds import close32_conditioned, fp32_drift
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -172,3 +173,92 @@ def test_dense_fp8_input_is_the_int8_problem():
             finally:
                 N.ising_destroy(h)
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+# ---------------------------------------------------------------------------
+# plain FP32 form (F32 iterates: FP32 products and accumulation on the CUDA cores)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n, R, kind", [(256, 32, "pm1"), (200, 5, "pm1"), (1500, 8, "pm1"), (384, 130, "pm1"),
+                                        (200, 20, "int"), (1500, 8, "int"), (384, 48, "pm1_sparse")])
+@pytest.mark.parametrize("iters", [1, 10])
+def test_dense_iterates_f32(n, R, kind, iters):
+    """FP32 iterates against the FP64 oracle: one step within the FP32 bar (1e-5 relative per
+    replica, every element within 1e-4 of the largest); ten steps under the conditioned FP32
+    bound with the dense step's rounding sqrt(n) 2^-24 (weakly stable replicas amplify it, see
+    fp32_bounds). Ragged n (not a
+    multiple of the 128-row tile or the 64-column stage), ragged R (scalar loads) and two
+    replica tiles (R = 130)."""
+    J = _jmat(kind, n, 93)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    x0 = I.x0_uniform(n, R, seed=94)
+    ref, drift = fp32_drift(O.Problem(J), x0, alpha, beta, iters, eps_step=np.sqrt(n) * 2.0 ** -24)
+    h = N.ising_create(N.Problem(J))
+    try:
+        x = torch.from_numpy(x0.copy()).cuda()
+        N.ising_iterate(h, x, [alpha], [beta], iters)
+        got = x.cpu().numpy().astype(np.float64)
+    finally:
+        N.ising_destroy(h)
+    if iters == 1:
+        assert _rel(got, ref).max() <= 1e-5, _rel(got, ref).max()
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    else:
+        close32_conditioned(got, ref, drift)
+
+
+def test_dense_f32_full_size_16384x256_sampled():
+    """n = 16384 dense +-1, R = 256 FP32 replicas: two sampled replicas recomputed by the
+    oracle, after 1 step within 1e-5, after 5 steps under the conditioned FP32 bound; the exact
+    energy of the device's own spins."""
+    n, R = 16384, 256
+    J = I.dense_pm1(n, seed=3)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="wigner")
+    x0 = I.x0_uniform(n, R, seed=3)
+    sample = [0, 201]
+    P = O.Problem(J)
+    h = N.ising_create(N.Problem(J))
+    try:
+        x = torch.from_numpy(x0.copy()).cuda()
+        N.ising_iterate(h, x, [alpha], [beta], 1)
+        ref1 = O.doch(P, x0[:, sample], alpha, beta, 1)
+        assert _rel(x.cpu().numpy()[:, sample].astype(np.float64), ref1).max() <= 1e-5
+        N.ising_iterate(h, x, [alpha], [beta], 4)
+        ref5, drift = fp32_drift(P, x0[:, sample], alpha, beta, 5, eps_step=np.sqrt(n) * 2.0 ** -24)
+        close32_conditioned(x.cpu().numpy()[:, sample].astype(np.float64), ref5, drift)
+        E = torch.zeros(R, dtype=torch.int64, device="cuda")
+        N.ising_energy(h, x, E_int=E)
+        Er, _ = O.energy_int(P, O.sign(x.cpu().numpy()[:, sample].astype(np.float64)))
+        assert np.array_equal(E.cpu().numpy()[sample], Er)
+    finally:
+        N.ising_destroy(h)
+
+
+def test_dense_bf16_and_f32_forms_reach_equal_final_energy():
+    """The low-precision form (BF16 state, tensor cores) against the plain FP32 form on the
+    same dense +-1 instance and the same 64 starts, 300 iterations each: per-replica basins may
+    differ (BF16 rounding of the state, 2^-9), so the comparison is of the energy distributions
+    over replicas -- mean within 1 %, best within 2 % -- and both forms' spins have exact
+    integer energies (checked against the oracle on four replicas)."""
+    n, R, iters = 2048, 64, 300
+    J = I.dense_pm1(n, seed=95)
+    alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
+    x0 = I.x0_uniform(n, R, seed=96)
+    P = O.Problem(J)
+    h = N.ising_create(N.Problem(J))
+    out = {}
+    try:
+        for name, x in (("bf16", torch.from_numpy(x0).to(torch.bfloat16).cuda()),
+                        ("f32", torch.from_numpy(x0.copy()).cuda())):
+            N.ising_iterate(h, x, [alpha], [beta], iters)
+            E = torch.zeros(R, dtype=torch.int64, device="cuda")
+            N.ising_energy(h, x, E_int=E)
+            s = O.sign(x.float().cpu().numpy().astype(np.float64))
+            out[name] = E.cpu().numpy()
+            Er, _ = O.energy_int(P, s[:, :4])
+            assert np.array_equal(out[name][:4], Er)
+    finally:
+        N.ising_destroy(h)
+    b, f = out["bf16"].astype(np.float64), out["f32"].astype(np.float64)
+    assert abs(b.mean() - f.mean()) <= 0.01 * abs(f.mean()), (b.mean(), f.mean())
+    assert abs(b.min() - f.min()) <= 0.02 * abs(f.min()), (b.min(), f.min())

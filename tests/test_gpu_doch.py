@@ -28,6 +28,7 @@ import oracle as O
 from paper_2509_01928_gb300 import _native as N
 from paper_2509_01928_gb300 import build as B
 from paper_2509_01928_gb300 import inputs as I
+from fp32_bounds import close32_conditioned, fp32_drift
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,28 +59,8 @@ def _close(x_gpu, x_ref, tol):
     assert el <= 10 * tol, f"element error {el:.3e} > {10 * tol}"
 
 
-def _fp32_drift(P, x0, alpha, beta, iters):
-    """Relative drift per replica of the oracle trajectory under one FP32
-    rounding per component and step (max over two seeded sign patterns)."""
-    ref = O.doch(P, x0, alpha, beta, iters)
-    a = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (iters,))
-    out = np.zeros(ref.shape[1])
-    for seed in (1, 2):
-        x = np.asarray(x0, dtype=np.float64)
-        for j in range(iters):
-            x = O.doch(P, x, a[j], beta, 1)
-            sg = I.signs(I.stream_seed(seed, 200 + j), 0, x.size).reshape(x.shape)
-            x = x * (1.0 + sg * 2.0 ** -24)
-        out = np.maximum(out, np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0))
-    return ref, out
-
-
-def _close32_conditioned(x_gpu, ref, drift):
-    x_gpu = np.asarray(x_gpu, dtype=np.float64).reshape(ref.shape)
-    rel = np.linalg.norm(x_gpu - ref, axis=0) / np.linalg.norm(ref, axis=0)
-    bound = np.maximum(TOL32, 16.0 * drift)
-    assert np.all(rel <= bound), f"replica error {rel.max():.3e} above its bound {bound[np.argmax(rel)]:.3e}"
-    assert np.median(rel) <= TOL32, f"median replica error {np.median(rel):.3e} > {TOL32}"
+_fp32_drift = fp32_drift
+_close32_conditioned = close32_conditioned
 
 
 class Handle:
@@ -457,3 +438,44 @@ def test_ell_input_runs_as_csr():
             finally:
                 N.ising_destroy(hd)
         assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-4])
+def test_batched_resident_variants_agree(eps, monkeypatch):
+    """Every variant of the shared-memory resident kernel the autotuner chooses from (512 or
+    1024 threads; both Jacobi copies in shared memory, or one copy with the new iterate through
+    global scratch, which doubles the replicas per item) computes the same arithmetic in the same
+    order: bit-identical iterates (and step counts under the stopping rule), and the oracle's
+    iterates within the FP32 bar. The second call of ising_iterate replays the captured graph."""
+    sizes, degrees = [400, 3000, 6000, 12000, 20000], [4, 9, 3, 10, 6]
+    gs, hs, J, h, off = _batch(sizes, degrees, seed=64)
+    J.val = J.val.astype(np.float32)
+    h = h.astype(np.float32)
+    R = 16
+    x0 = I.x0_uniform(int(off[-1]), R, seed=65)
+    alphas, betas = zip(*[O.alpha_beta(g, eta=1.0, method="wigner") for g in gs])
+    iters = 14
+    outs = []
+    for variant in ("1024:2", "1024:1", "512:2", "512:1"):
+        monkeypatch.setenv("ISING_RESIDENT_VARIANT", variant)
+        with Handle(J, h, off) as hd:
+            x = _dev(x0)
+            if eps > 0:
+                steps = np.zeros((len(gs), R), np.int32)
+                N.ising_iterate_until(hd, x, list(alphas), list(betas), iters, eps, steps=steps)
+                outs.append((x.cpu().numpy(), steps))
+            else:
+                N.ising_iterate(hd, x, list(alphas), list(betas), iters, n_instances=len(gs))
+                x2 = _dev(x0)
+                N.ising_iterate(hd, x2, list(alphas), list(betas), iters, n_instances=len(gs))  # graph replay
+                assert np.array_equal(x.cpu().numpy(), x2.cpu().numpy())
+                outs.append((x.cpu().numpy(), None))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        if eps > 0:
+            assert np.array_equal(o[1], outs[0][1])
+    if eps == 0:
+        xg = outs[0][0]
+        for b, g in enumerate(gs):
+            ref = O.doch(O.Problem(g, hs[b].astype(np.float32)), x0[off[b]:off[b + 1]], alphas[b], betas[b], iters)
+            _close(xg[off[b]:off[b + 1]], ref, TOL32)

@@ -7,6 +7,7 @@ import pytest
 import oracle as O
 from paper_2509_01928_gb300 import _native as N
 from paper_2509_01928_gb300 import build as B
+from oracle import matrices as M
 from paper_2509_01928_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -28,7 +29,7 @@ def test_s5_device_equals_reference(n, p, seed):
         rp, col, val = N.ising_csr_export(h)
     finally:
         N.ising_destroy(h)
-    J = I.s5_csr(n, p, seed)
+    J = M.s5_csr(n, p, seed)
     assert np.array_equal(rp, J.row_ptr)
     assert np.array_equal(col, J.col)
     assert np.array_equal(val.astype(np.int64), J.val.astype(np.int64))
@@ -36,7 +37,7 @@ def test_s5_device_equals_reference(n, p, seed):
 
 @pytest.mark.parametrize("method", [1, 2])
 def test_device_params_match_host_rule(method):
-    J = I.s5_csr(1500, 3.0, seed=6)
+    J = M.s5_csr(1500, 3.0, seed=6)
     ha, hb = N.ising_default_params(N.Problem(J), eta=1.0, method=method)
     h = N.ising_create_s5(1500, 3.0, 6)
     try:
@@ -59,7 +60,7 @@ def test_device_params_match_host_rule(method):
 
 def test_doch_on_device_generated_problem():
     n, p = 600, 4.0
-    J = I.s5_csr(n, p, seed=8)
+    J = M.s5_csr(n, p, seed=8)
     alpha, beta = O.alpha_beta(J, eta=1.0, method="eig")
     x0 = I.x0_uniform(n, 4, seed=9, dtype=np.float64)
     ref = O.doch(O.Problem(J), x0, alpha, beta, 60)
@@ -83,7 +84,7 @@ def test_device_params_match_oracle(method, omethod, tol):
     """ising_params_device against the oracle's Eq. alphabeta: the power method
     on the device against a dense symmetric eigensolver (to the power method's
     convergence, 1e-6), the Wigner estimate of Eq. estimate_eig_J to 1e-12."""
-    J = I.s5_csr(1500, 3.0, seed=6)
+    J = M.s5_csr(1500, 3.0, seed=6)
     ao, bo = O.alpha_beta(J, eta=1.0, method=omethod)
     h = N.ising_create_s5(1500, 3.0, 6)
     try:

@@ -3,6 +3,7 @@ J_ij = sin(i j + c), 1-based, J_ii = 0) against facts fixed by mathematics."""
 import numpy as np
 
 import oracle as O
+from oracle import matrices as M
 from paper_2509_01928_gb300 import inputs as I
 
 
@@ -35,6 +36,6 @@ def test_rows_of_unit_vectors_pick_single_couplings():
 def test_rows_agree_with_the_dense_product():
     n, c = 700, 100
     x = I.x0_uniform(n, 4, seed=71, dtype=np.float64)
-    full = O.coupling_product(O.Problem(I.procedural_sin(n, c)), x)
+    full = O.coupling_product(O.Problem(M.procedural_sin(n, c)), x)
     rows = [0, 5, 255, 256, 511, n - 1]
     np.testing.assert_allclose(O.procedural_rows(n, c, rows, x), full[rows], rtol=0, atol=1e-12)

@@ -4,11 +4,11 @@ argument reduction, floor(2^96 / (2 pi)), against a high-precision value."""
 import numpy as np
 import pytest
 
-from paper_2509_01928_gb300 import inputs as I
+from oracle import matrices as M
 
 
 def test_procedural_reference_matrix():
-    J = I.procedural_sin(50)
+    J = M.procedural_sin(50)
     assert J.shape == (50, 50) and np.array_equal(J, J.T) and np.all(np.diag(J) == 0)
     assert J[0, 1] == np.sin(1 * 2 + 100.0) and J[9, 3] == np.sin(10 * 4 + 100.0)
 

@@ -1,9 +1,10 @@
-"""Algorithm S5 (Supplementary Note 9) reference generator in inputs.py: the
+"""Algorithm S5 (Supplementary Note 9) reference generator (oracle/matrices.py): the
 vectorised generator against a literal pair-by-pair loop in Python integers,
 the exact threshold form of the test z < 1023, and the distribution the
 algorithm implies (density 1022 / N_p, values uniform on -510 .. 511)."""
 import numpy as np
 
+from oracle import matrices as M
 from paper_2509_01928_gb300 import inputs as I
 
 
@@ -33,7 +34,7 @@ def _literal(n, p, seed):
 
 def test_s5_matches_literal_loop():
     for n, p, seed in ((40, 30.0, 11), (64, 100.0, 3), (90, 7.5, 5)):
-        J = I.s5_csr(n, p, seed)
+        J = M.s5_csr(n, p, seed)
         d, present = _literal(n, p, seed)
         got = np.zeros((n, n), dtype=bool)
         rows = np.repeat(np.arange(n), np.diff(J.row_ptr))
@@ -46,25 +47,25 @@ def test_s5_matches_literal_loop():
 def test_s5_n_p_is_the_rounded_quotient():
     """N_p of p = 0.05 is 2046000 (102300 / 0.05 in decimal): the rounded double
     quotient, whose floor Python's float floor division would put at 2045999."""
-    assert I.s5_params(0.05)[0] == 2046000
-    assert I.s5_params(100.0)[0] == 1023 and I.s5_params(0.5)[0] == 204600
+    assert M.s5_params(0.05)[0] == 2046000
+    assert M.s5_params(100.0)[0] == 1023 and M.s5_params(0.5)[0] == 204600
 
 
 def test_s5_threshold_is_exact():
     rng = np.random.default_rng(0)
     for p in (100.0, 50.0, 3.3, 0.01, 1e-6):
-        n_p, thr = I.s5_params(p)
+        n_p, thr = M.s5_params(p)
         us = [int(v) for v in rng.integers(0, 2**63, 2000, dtype=np.int64)] + [thr - 1, thr, thr + 1, 0, 2**64 - 1]
         for u in us:
             u %= 1 << 64
             assert (u < thr) == (1 + (u * n_p >> 64) < 1023)
-        assert int(I._mulhi64(np.array([thr - 1], np.uint64), n_p)[0]) == ((thr - 1) * n_p) >> 64
+        assert int(M._mulhi64(np.array([thr - 1], np.uint64), n_p)[0]) == ((thr - 1) * n_p) >> 64
 
 
 def test_s5_distribution():
     n, p = 3000, 2.0
-    J = I.s5_csr(n, p, seed=21)
-    n_p, _ = I.s5_params(p)
+    J = M.s5_csr(n, p, seed=21)
+    n_p, _ = M.s5_params(p)
     pairs = n * (n - 1) // 2
     kept = J.nnz // 2
     mean = pairs * 1022 / n_p
