@@ -44,6 +44,7 @@ SEED = 2
 # right and down couplings (2 B) and writes x (4 B) once per site: 10 B per site per launch,
 # 5 B per site-update.
 BYTES_PER_SITE = 10
+STEPS_PER_LAUNCH = 2
 DOMINANT = "torus_f32_r1_vec4_t2"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "torus_f32_r1_vec4_t2_10000x10000.md")
 
@@ -222,6 +223,7 @@ class Torus:
         self.L, self.iters, self.R = args.size, args.iters, 1
         self.n = self.L * self.L
         t = I.torus_pm1(self.L, self.L, seed=SEED + 1000 * rank)
+        self.t = t
         self.x0 = I.x0_uniform(self.n, 1, seed=SEED + 1000 * rank)
         prob = N.Problem(t)
         self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
@@ -234,7 +236,7 @@ class Torus:
         self.best = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.units = float(self.n) * self.R * self.iters
         # two steps per lattice launch (an odd count ends with one single step)
-        self.dominant_launches = self.iters // 2 + self.iters % 2
+        self.dominant_launches = self.iters // STEPS_PER_LAUNCH + (1 if self.iters % STEPS_PER_LAUNCH else 0)
         self.launches = self.dominant_launches + 3
         self.config = {"workload": f"torus2d {self.L}x{self.L} +-1 int8 couplings, FP32 iterates, R=1, "
                                    f"{self.iters} DOCH iterations + sign + int64 energy/cut + best replica",
@@ -258,7 +260,7 @@ class Torus:
         ach = alg / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": recorded_traffic(), "kernel": self.dominant, "peak_kind": kind,
-                "algorithmic_bytes_per_launch": alg, "doch_steps_per_launch": 2}
+                "algorithmic_bytes_per_launch": alg, "doch_steps_per_launch": STEPS_PER_LAUNCH}
 
     def e2e(self, n_steps, sid):
         N = self.N
@@ -273,10 +275,40 @@ class Torus:
             "ising_iterate + ising_energy on pinned host arrays, each step continues from the last"
 
     def cpu_baseline(self, args):
-        lr = lc = args.ref_size
-        u, dt = cpu_oracle_sample(lr, lc, args.cpu_iters)
-        return {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"torus {lr}x{lc} int8 +-1, {args.cpu_iters} FP64 DOCH iterations + sign + int64 energy"}
+        """The oracle on a bounded sample of the timed lattice itself: x^(iters) of a 16 x 16 block
+        of sites depends only on the sites within `iters` lattice steps, so the oracle runs all
+        iterations on that light-cone patch (open boundaries, the lattice's own couplings) -- timed
+        as the CPU baseline -- and its block is compared with the GPU's final iterate there."""
+        import oracle as O
+        from oracle.lattice import light_cone_patch
+        size, it = 16, self.iters
+        if 2 * it + size > self.L:
+            lr = lc = args.ref_size
+            u, dt = cpu_oracle_sample(lr, lc, args.cpu_iters)
+            return {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"torus {lr}x{lc} int8 +-1, {args.cpu_iters} FP64 DOCH iterations"}
+        r0 = c0 = 7 * 120 - 8  # straddles a column segment of the multi-step kernels
+        J, G = light_cone_patch(self.t, r0, c0, size, it)
+        P = size + 2 * it
+        t0 = time.perf_counter()
+        ref = O.doch(O.Problem(J), self.x0.ravel()[G].astype(np.float64), float(self.alpha[0]),
+                     float(self.beta[0]), it).reshape(P, P)
+        dt = time.perf_counter() - t0
+        blk = ref[it:it + size, it:it + size].ravel()
+        sites = G.reshape(P, P)[it:it + size, it:it + size].ravel()
+        got = self.x.cpu().numpy().ravel()[sites].astype(np.float64)
+        rel = float(np.linalg.norm(got - blk) / np.linalg.norm(blk))
+        el = float(np.abs(got - blk).max() / np.abs(blk).max())
+        return {"value": P * P * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the light-cone patch ({P}x{P} sites, open boundaries) of a {size}x{size} block of the "
+                          f"timed lattice, {it} FP64 DOCH iterations",
+                "oracle_match": {"sites": size * size, "iters": it, "rel_err": rel, "max_element_err": el,
+                                 "bound": 1e-5, "ok": rel <= 1e-5 and el <= 1e-4,
+                                 "what": "the GPU's x^(iters) of the timed run against the oracle at those sites"}}
+
+    def energy(self):
+        E, cut = int(self.E.item()), int(self.cut.item())
+        return {"E": E, "cut": cut, "E_per_spin": E / self.n, "exact": "int64, sign(x^(iters))"}
 
     def close(self):
         self.N.ising_destroy(self.h)
@@ -341,6 +373,11 @@ class Dense:
         dt = time.perf_counter() - w0
         nb = self.n * self.R * 2
         return dt, 2 * nb, nb + 8 * self.R, "ising_iterate + ising_energy on pinned host BF16 arrays"
+
+    def energy(self):
+        E = self.E.cpu().numpy().astype(np.float64)
+        return {"E_best": float(E.min()), "E_mean": float(E.mean()), "E_std": float(E.std()),
+                "replicas": int(E.size), "exact": "int64, sign(x^(iters))"}
 
     def cpu_baseline(self, args):
         import oracle as O
@@ -447,6 +484,13 @@ class Precision:
             f["iters_to_equal_energy"] = hit
             f["s_to_equal_energy"] = None if hit is None else sec * hit / self.iters
         b, f = forms["bf16_tensor_cores"], forms["f32_cuda_cores"]
+        # the FP32 form on the CUDA cores: 2 n^2 R FP32 flops per iteration against the derived FP32 FMA
+        # peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz, the maximum SM clock)
+        flops = 2.0 * self.n * self.n * self.R
+        f_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        f_ach = flops / (f["ms_per_iteration"] / 1e3) / 1e12
+        f["roofline"] = {"bound": "alu", "achieved": f_ach, "peak": f_peak, "unit": "TFLOP/s", "frac": f_ach / f_peak,
+                         "kernel": "dense_f32_step", "peak_kind": "derived: FP32 FMA lanes x max SM clock"}
         return {"forms": forms,
                 "equal_energy": {"target_mean_E": target, "tol": self.tol,
                                  "mean_E_rel_diff": (b["E_mean"] - f["E_mean"]) / abs(f["E_mean"]),
@@ -466,6 +510,9 @@ class Precision:
 
     def e2e(self, n_steps, sid):
         return Dense.e2e(self, n_steps, sid)
+
+    def energy(self):
+        return Dense.energy(self)
 
     def cpu_baseline(self, args):
         return Dense.cpu_baseline(self, args)
@@ -610,13 +657,13 @@ class Backward:
     def roofline(self, per_launch_s):
         # per step index k the call runs a forward step, a recompute step and an adjoint step; unique
         # bytes: forward and recompute read and write x (2 n R 4 B each) and read the CSR arrays; the
-        # adjoint reads g^(k+1), x^(k+1), x^k and writes g^k (4 n R 4 B) and reads the CSR arrays.
+        # adjoint reads w^k and x^k and writes w^(k-1) (3 n R 4 B) and reads the CSR arrays.
         # The 25.6 MB iterates stay in L2, so this is the HBM-equivalent rate of the whole step triple.
         peak, kind = measured_peaks()
         nnz = 3 * self.n
         csr = nnz * (4 + 1) + (self.n + 1) * 8
         xb = self.n * self.R * 4
-        alg = 2 * (2 * xb + csr) + (4 * xb + csr)
+        alg = 2 * (2 * xb + csr) + (3 * xb + csr)
         ach = alg / per_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "kernel": "csr_step_kernel (forward, recompute) + adjoint_step_kernel",
@@ -743,6 +790,7 @@ class Adoch:
         self.L, self.iters, self.R, self.q = args.size, args.adoch_iters, 1, 5
         self.n = self.L * self.L
         t = I.torus_pm1(self.L, self.L, seed=SEED + 1000 * rank)
+        self.t = t
         self.x0 = I.x0_uniform(self.n, 1, seed=SEED + 1000 * rank)
         prob = N.Problem(t)
         self.alpha, self.beta = N.ising_default_params(prob, eta=1.0, method=2)
@@ -1081,6 +1129,8 @@ def run_ours(args):
     }
     if extra is not None:
         line["precision"] = extra
+    if hasattr(wl, "energy"):
+        line["energy"] = wl.energy()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -1,12 +1,14 @@
-"""Light-cone patches of a periodic lattice (test helper, no method arithmetic).
+"""Light-cone patches of a periodic lattice -- oracle inputs, TEST INFRASTRUCTURE ONLY
+(no method arithmetic; only the tests and the benchmark's CPU legs use it).
 
 After N Jacobi steps of Eq. FPE the iterate of a lattice site depends only on
 the sites within N lattice steps of it. So x^(N) on a block of sites can be
 computed from the open-boundary sub-lattice that extends the block by N sites
 in every direction: every site within N - 1 steps of the block has all of its
 neighbours inside that patch. This module lays out such a patch as CSR with
-the lattice's own couplings; tests/test_lattice_patch.py checks it against
-the full lattice on the CPU.
+the lattice's own couplings; the oracle run on that patch gives x^(N) of the
+block's sites of the full lattice (checked against the full lattice on the
+CPU by the test suite).
 """
 import numpy as np
 

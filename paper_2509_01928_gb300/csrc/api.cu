@@ -1199,8 +1199,25 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
             const bool pairs_ok = !Hd && c->format == ISING_FMT_TORUS2D && xtype == ISING_F32 &&
                                   !(c->flags & ISING_FLAG_SINGLE_STEP) &&
                                   torus_pair_ok(c, static_cast<const float *>(cur), static_cast<const float *>(nxt), R);
+            // steps per lattice pass: at most 2 (default) or ISING_LATTICE_PASS = 1, 2 or 3
+            int per_pass = 2;
+            if (const char *env = std::getenv("ISING_LATTICE_PASS")) {
+                const int v = std::atoi(env);
+                if (v >= 1 && v <= 3) per_pass = v;
+            }
+            const bool triples_ok = pairs_ok && per_pass >= 3 && c->l_rows >= 6;
             for (int k = 0; k < iters;) {
-                if (pairs_ok && k + 1 < iters) {  // two steps in one pass over the lattice
+                if (triples_ok && k + 2 < iters) {  // three steps in one pass over the lattice
+                    const double a1 = alpha_h[alpha_len == 1 ? 0 : k], a2 = alpha_h[alpha_len == 1 ? 0 : k + 1],
+                                 a3 = alpha_h[alpha_len == 1 ? 0 : k + 2];
+                    DOCH_CHECK(torus_triple_f32(c, static_cast<const float *>(cur), static_cast<float *>(nxt),
+                                                static_cast<float>(a1), static_cast<float>(a2), static_cast<float>(a3),
+                                                1.0 / beta_h[0], st));
+                    std::swap(cur, nxt);
+                    k += 3;
+                    continue;
+                }
+                if (pairs_ok && per_pass >= 2 && k + 1 < iters) {  // two steps in one pass over the lattice
                     const double a1 = alpha_h[alpha_len == 1 ? 0 : k], a2 = alpha_h[alpha_len == 1 ? 0 : k + 1];
                     DOCH_CHECK(torus_pair_f32(c, static_cast<const float *>(cur), static_cast<float *>(nxt),
                                               static_cast<float>(a1), static_cast<float>(a2), 1.0 / beta_h[0], st));
@@ -1208,8 +1225,25 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
                     k += 2;
                     continue;
                 }
-                if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
-                DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+                // H monitor fused into the step where the step kernel supports it (the exact
+                // separate FP64 reduction for FP32 iterates under ISING_FLAG_STRICT_MONOTONE)
+                bool fused = false;
+                if (Hd && !(xtype == ISING_F32 && (c->flags & ISING_FLAG_STRICT_MONOTONE))) {
+                    const double ak = alpha_h[alpha_len == 1 ? 0 : k];
+                    double *Hk = Hd + static_cast<size_t>(k) * pairs;
+                    ising_status_t fs = ISING_ERR_UNSUPPORTED;
+                    if (c->format == ISING_FMT_CSR)
+                        fs = csr_step_traced(c, cur, nxt, xtype, R, p, k, ak, beta_h[0], Hk, st);
+                    else if (c->format == ISING_FMT_TORUS2D && xtype == ISING_F32)
+                        fs = torus_step_f32_traced(c, static_cast<const float *>(cur), static_cast<float *>(nxt), R,
+                                                   static_cast<float>(ak), 1.0 / beta_h[0], ak, beta_h[0], Hk, st);
+                    if (fs != ISING_OK && fs != ISING_ERR_UNSUPPORTED) return fs;
+                    fused = fs == ISING_OK;
+                }
+                if (!fused) {
+                    if (Hd) DOCH_CHECK(hamiltonian_reduce(c, cur, xtype, R, p, k, Hd + static_cast<size_t>(k) * pairs, st));
+                    DOCH_CHECK(step(c, cur, nxt, xtype, R, p, alpha_h, beta_h, k, st));
+                }
                 std::swap(cur, nxt);
                 ++k;
             }

@@ -198,6 +198,10 @@ ising_status_t torus_step_f64(const ising_context *c, const double *x_in, double
 bool torus_pair_ok(const ising_context *c, const float *x_in, const float *x_out, int R);
 ising_status_t torus_pair_f32(const ising_context *c, const float *x_in, float *x_out, float alpha1,
                               float alpha2, double inv_beta, cudaStream_t st);
+// TORUS2D, three DOCH steps in one pass (alpha1, alpha2, alpha3), same conditions
+// as the two-step pass and l_rows >= 6.
+ising_status_t torus_triple_f32(const ising_context *c, const float *x_in, float *x_out, float alpha1, float alpha2,
+                                float alpha3, double inv_beta, cudaStream_t st);
 
 // Per-instance parameter tables on the device (filled by ising_iterate):
 // alpha [n_inst][alpha_len] and beta [n_inst] in FP64, plus FP32 copies of
@@ -217,6 +221,18 @@ struct ParamTabs {
 // CSR, one DOCH step for all instances (alpha of step k), xtype F32 or F64.
 ising_status_t csr_step(const ising_context *c, const void *x_in, void *x_out, int xtype, int R,
                         const ParamTabs &p, int k, cudaStream_t st);
+// The same step with the H monitor fused (one instance): H(x^(k)) of Eq. Hamilton
+// per replica into H_out [R] (device), alpha_k and beta of the step.
+// ISING_ERR_UNSUPPORTED when the fused form does not apply (batched instances,
+// R / vector width > 256).
+ising_status_t csr_step_traced(ising_context *c, const void *xi, void *xo, int xtype, int R, const ParamTabs &p,
+                               int k, double alpha_k, double beta, double *H_out, cudaStream_t st);
+// TORUS2D single step (R = 1, FP32 fast path) with the fused H monitor; UNSUPPORTED otherwise.
+ising_status_t torus_step_f32_traced(ising_context *c, const float *x_in, float *x_out, int R, float alpha,
+                                     double inv_beta, double alpha_k, double beta, double *H_out, cudaStream_t st);
+// H per replica from fused per-block partials [blocks][R][4] (x^4, x^2, x u, h x)
+ising_status_t ham_fused_finish_launch(const double *hpart, int blocks, int R, double alpha, double beta, double *H,
+                                       cudaStream_t st);
 // CSR, all `iters` steps in one launch: one CTA per (instance, replica) with
 // the iterate in shared memory. ISING_ERR_UNSUPPORTED when an instance does
 // not fit (the caller then uses csr_step).

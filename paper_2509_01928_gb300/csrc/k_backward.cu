@@ -33,6 +33,7 @@ namespace doch {
 namespace {
 
 constexpr int kBThreads = 256;
+constexpr int kBatchB = 4;  // entries whose loads are issued together
 
 template <int V> struct F4;
 template <> struct F4<1> { using type = float; };
@@ -113,12 +114,25 @@ loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__
 #pragma unroll
         for (int q = 0; q < V; ++q) u[q] = XT(0);
         const int64_t e1 = __ldg(row_ptr + i + 1);
-        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
-            const XT wv = static_cast<XT>(__ldg(val + e));
-            XT xv[V];
-            ld<V>(x + static_cast<int64_t>(__ldg(col + e)) * R + ch * V, xv);
+        for (int64_t e = __ldg(row_ptr + i); e < e1; e += kBatchB) {
+            const int cnt = e1 - e < kBatchB ? static_cast<int>(e1 - e) : kBatchB;
+            int64_t js[kBatchB];
+            XT ws[kBatchB];
 #pragma unroll
-            for (int q = 0; q < V; ++q) u[q] += wv * xv[q];
+            for (int t = 0; t < kBatchB; ++t) {
+                js[t] = t < cnt ? __ldg(col + e + t) : 0;
+                ws[t] = t < cnt ? static_cast<XT>(__ldg(val + e + t)) : XT(0);
+            }
+            XT xv[kBatchB][V];
+#pragma unroll
+            for (int t = 0; t < kBatchB; ++t)
+                if (t < cnt) ld<V>(x + js[t] * R + ch * V, xv[t]);
+#pragma unroll
+            for (int t = 0; t < kBatchB; ++t)
+                if (t < cnt) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) u[q] += ws[t] * xv[t][q];
+                }
         }
         XT xi[V];
         float wi[V];
@@ -165,13 +179,27 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
 #pragma unroll
         for (int q = 0; q < V; ++q) acc[q] = 0.f;
         const int64_t e1 = __ldg(row_ptr + i + 1);
-        for (int64_t e = __ldg(row_ptr + i); e < e1; ++e) {
-            const int64_t j = __ldg(col + e);
-            const float wv = static_cast<float>(__ldg(val + e));
-            float wj[V];
-            ld<V>(w_in + j * R + ch * V, wj);
+        // entries in batches (the last one partial): index/value loads, then the gathers, then
+        // the products in entry order
+        for (int64_t e = __ldg(row_ptr + i); e < e1; e += kBatchB) {
+            const int cnt = e1 - e < kBatchB ? static_cast<int>(e1 - e) : kBatchB;
+            int64_t js[kBatchB];
+            float ws[kBatchB];
 #pragma unroll
-            for (int q = 0; q < V; ++q) acc[q] += wv * wj[q];
+            for (int t = 0; t < kBatchB; ++t) {
+                js[t] = t < cnt ? __ldg(col + e + t) : 0;
+                ws[t] = t < cnt ? static_cast<float>(__ldg(val + e + t)) : 0.f;
+            }
+            float wj[kBatchB][V];
+#pragma unroll
+            for (int t = 0; t < kBatchB; ++t)
+                if (t < cnt) ld<V>(w_in + js[t] * R + ch * V, wj[t]);
+#pragma unroll
+            for (int t = 0; t < kBatchB; ++t)
+                if (t < cnt) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[q] += ws[t] * wj[t][q];
+                }
         }
         float wi[V], out[V];
         XT xc[V];

@@ -13,6 +13,7 @@
 // __syncthreads(); the CSR arrays stream through L1/L2.
 #include <algorithm>
 
+#include "hamsum.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -68,21 +69,27 @@ __device__ __forceinline__ void stv(T *p, const T (&v)[V]) {
 
 constexpr int kCsrBatch = 8;  // entries whose loads are issued together
 
-template <typename XT, typename VT, int V>
+// H monitor fused into the step (TRACE, one instance): the step already holds
+// u = J x^(k) and x^(k), so it also sums the terms of H(x^(k)) (Eq. Hamilton,
+// -h^T x for a field): x^4, x^2, x u, h x per replica. FP64 iterates sum in
+// FP64; FP32 iterates form the terms in FP32 and sum them per thread with a
+// compensated (Kahan) FP32 sum. Each block writes FP64 partials
+// hpart[block][R][4], summed over threads in a fixed order.
+template <typename XT, typename VT, int V, bool TRACE>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
                 const int64_t *__restrict__ inst_off, int n_inst, int64_t n, int R,
                 const XT *__restrict__ alpha_tab, int alpha_len, int k,
-                const XT *__restrict__ beta_tab) {
+                const XT *__restrict__ beta_tab, double *__restrict__ hpart) {
     const int C = R / V;
     const int ak = alpha_len == 1 ? 0 : k;
     // each thread keeps one replica chunk and strides over rows: no division in the loop
     const int rows_per_block = blockDim.x / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
-    if (rl >= rows_per_block) return;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; i < n;
+    HamSum<XT> hs[TRACE ? V : 1][4];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; rl < rows_per_block && i < n;
          i += static_cast<int64_t>(gridDim.x) * rows_per_block) {
         const int b = n_inst > 1 ? find_inst(inst_off, n_inst, i) : 0;
         const XT a = alpha_tab[static_cast<int64_t>(b) * alpha_len + ak];
@@ -124,6 +131,36 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
 #pragma unroll
         for (int q = 0; q < V; ++q) out[q] = dcbrt(scale_beta(acc[q] + a * xs[q] + hi, bb));
         stv<XT, V>(xo + i * R + ch * V, out);
+        if constexpr (TRACE) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const XT x2 = xs[q] * xs[q];
+                hs[q][0].add(x2 * x2);
+                hs[q][1].add(x2);
+                hs[q][2].add(xs[q] * acc[q]);
+                hs[q][3].add(hi * xs[q]);
+            }
+        }
+    }
+    if constexpr (TRACE) {
+        // per replica: threads of the same chunk ch (rows rl = 0 .. rows_per_block-1) in row order
+        __shared__ double red[256][4];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) red[threadIdx.x][m] = hs[q][m].value();
+            __syncthreads();
+            if (rl == 0) {
+                double t[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int r2 = 0; r2 < rows_per_block; ++r2)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) t[m] += red[r2 * C + ch][m];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    hpart[(static_cast<int64_t>(blockIdx.x) * R + ch * V + q) * 4 + m] = t[m];
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -233,31 +270,42 @@ csr_fused_cluster(XT *__restrict__ x, const int64_t *__restrict__ row_ptr, const
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) x[(lo + i) * R + r] = cur[i];
 }
 
-template <typename XT, typename VT, int V>
-void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
-                 const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, cudaStream_t st) {
-    const int C = R / V;
+int step_blocks(const ising_context *c, int C) {
     const int rows_per_block = C <= 256 ? 256 / C : 1;
     int64_t blocks = (c->n + rows_per_block - 1) / rows_per_block;
     const int64_t cap = static_cast<int64_t>(c->num_sms) * 32;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    return static_cast<int>(blocks);
+}
+
+template <typename XT, typename VT, int V>
+void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
+                 const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, double *hpart, cudaStream_t st) {
+    const int C = R / V;
+    const int blocks = step_blocks(c, C);
     const int threads = C <= 256 ? 256 : ((C + 31) / 32) * 32;
-    csr_step_kernel<XT, VT, V><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
-        xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
-        c->n, R, alpha_tab, alpha_len, k, beta_tab);
+    if (hpart)
+        csr_step_kernel<XT, VT, V, true><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
+            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
+            c->n, R, alpha_tab, alpha_len, k, beta_tab, hpart);
+    else
+        csr_step_kernel<XT, VT, V, false><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
+            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
+            c->n, R, alpha_tab, alpha_len, k, beta_tab, nullptr);
 }
 
 template <typename XT, int V>
 ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
-                            const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab,
+                            const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, double *hpart,
                             cudaStream_t st) {
     if (R / V > 1024) return fail(ISING_ERR_UNSUPPORTED, "CSR step: R / vector width must be <= 1024");
+    if (hpart && R / V > 256) return ISING_ERR_UNSUPPORTED;  // the fused monitor needs one row per 256 threads
     switch (c->jtype) {
-        case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
-        case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
-        case ISING_F32: launch_step<XT, float, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
-        case ISING_F64: launch_step<XT, double, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, st); break;
+        case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
+        case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
+        case ISING_F32: launch_step<XT, float, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
+        case ISING_F64: launch_step<XT, double, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
         default: return fail(ISING_ERR_UNSUPPORTED, "CSR value type not supported on the device");
     }
     DOCH_CUDA(cudaGetLastError());
@@ -355,26 +403,55 @@ size_t csr_fused_max_spins(int xtype) {
     return static_cast<size_t>(optin) / (2 * (xtype == ISING_F64 ? 8 : 4));
 }
 
-ising_status_t csr_step(const ising_context *c, const void *xi, void *xo, int xtype, int R,
-                        const ParamTabs &p, int k, cudaStream_t st) {
+static ising_status_t csr_step_impl(const ising_context *c, const void *xi, void *xo, int xtype, int R,
+                                    const ParamTabs &p, int k, double *hpart, int *blocks, cudaStream_t st) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(xi) | reinterpret_cast<uintptr_t>(xo);
     if (xtype == ISING_F32) {
         const float *x_in = static_cast<const float *>(xi);
         float *x_out = static_cast<float *>(xo);
-        if (R % 4 == 0 && a % 16 == 0)
-            return dispatch_val<float, 4>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
-        if (R % 2 == 0 && a % 8 == 0)
-            return dispatch_val<float, 2>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
-        return dispatch_val<float, 1>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, st);
+        if (R % 4 == 0 && a % 16 == 0) {
+            *blocks = step_blocks(c, R / 4);
+            return dispatch_val<float, 4>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f,
+                                          hpart, st);
+        }
+        if (R % 2 == 0 && a % 8 == 0) {
+            *blocks = step_blocks(c, R / 2);
+            return dispatch_val<float, 2>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f,
+                                          hpart, st);
+        }
+        *blocks = step_blocks(c, R);
+        return dispatch_val<float, 1>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, hpart,
+                                      st);
     }
     if (xtype == ISING_F64) {
         const double *x_in = static_cast<const double *>(xi);
         double *x_out = static_cast<double *>(xo);
-        if (R % 2 == 0 && a % 16 == 0)
-            return dispatch_val<double, 2>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, st);
-        return dispatch_val<double, 1>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, st);
+        if (R % 2 == 0 && a % 16 == 0) {
+            *blocks = step_blocks(c, R / 2);
+            return dispatch_val<double, 2>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, hpart,
+                                           st);
+        }
+        *blocks = step_blocks(c, R);
+        return dispatch_val<double, 1>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, hpart, st);
     }
     return fail(ISING_ERR_UNSUPPORTED, "CSR iterate type must be F32 or F64");
+}
+
+ising_status_t csr_step(const ising_context *c, const void *xi, void *xo, int xtype, int R,
+                        const ParamTabs &p, int k, cudaStream_t st) {
+    int blocks = 0;
+    return csr_step_impl(c, xi, xo, xtype, R, p, k, nullptr, &blocks, st);
+}
+
+ising_status_t csr_step_traced(ising_context *c, const void *xi, void *xo, int xtype, int R, const ParamTabs &p,
+                               int k, double alpha_k, double beta, double *H_out, cudaStream_t st) {
+    if (c->n_inst != 1) return ISING_ERR_UNSUPPORTED;
+    const size_t max_blocks = static_cast<size_t>(c->num_sms) * 32;  // the cap of step_blocks
+    DOCH_CHECK(c->partials.ensure(sizeof(double) * 4 * static_cast<size_t>(R) * max_blocks));
+    int blocks = 0;
+    const ising_status_t s = csr_step_impl(c, xi, xo, xtype, R, p, k, c->partials.as<double>(), &blocks, st);
+    if (s != ISING_OK) return s;
+    return ham_fused_finish_launch(c->partials.as<double>(), blocks, R, alpha_k, beta, H_out, st);
 }
 
 ising_status_t csr_fused(const ising_context *c, void *x, int xtype, int R, const ParamTabs &p,

@@ -185,6 +185,18 @@ __global__ void energy_finish(const Acc *__restrict__ partials, int pairs, int c
     }
 }
 
+// H(x^(k)) per replica from the fused monitor's partials [block][R][4], blocks in order
+__global__ void ham_fused_finish(const double *__restrict__ hpart, int blocks, int R, double alpha, double beta,
+                                 double *__restrict__ H) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < blocks; ++b)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) t[m] += hpart[(static_cast<int64_t>(b) * R + r) * 4 + m];
+    H[r] = beta / 4.0 * t[0] - alpha / 2.0 * t[1] - 0.5 * t[2] - t[3];
+}
+
 __global__ void ham_finish(const double *__restrict__ partials, int n_inst, int R, int chunks,
                            const double *__restrict__ alpha_tab, int alpha_len, int k,
                            const double *__restrict__ beta_tab, double *__restrict__ H) {
@@ -336,6 +348,13 @@ ising_status_t hamiltonian_reduce(ising_context *c, const void *x, int xtype, in
     const int pairs = c->n_inst * R;
     ham_finish<<<(pairs + 127) / 128, 128, 0, st>>>(c->partials.as<double>(), c->n_inst, R, chunks,
                                                     p.alpha_d, p.alpha_len, k, p.beta_d, H_out);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+ising_status_t ham_fused_finish_launch(const double *hpart, int blocks, int R, double alpha, double beta, double *H,
+                                       cudaStream_t st) {
+    ham_fused_finish<<<(R + 127) / 128, 128, 0, st>>>(hpart, blocks, R, alpha, beta, H);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "cbrt.cuh"
+#include "hamsum.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -92,16 +93,58 @@ __device__ __forceinline__ float4 row4_new(float4 xm, float xl, float xr, float4
     return row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha, zscale, xscale);
 }
 
-// 40 registers: 6 CTAs (1536 threads) per SM keep enough loads in flight
-__global__ void __launch_bounds__(kThreads, 6)
+// u of four consecutive sites (the sums row4_new_w feeds to site_new)
+__device__ __forceinline__ float4 row4_u(float4 xm, float xl, float xr, float4 xu, float4 xd, const float (&wr)[4],
+                                         float wleft, const float (&dd)[4], const float (&du)[4]) {
+    float4 u;
+    u.x = site_sum(wr[0], xm.y, wleft, xl, dd[0], xd.x, du[0], xu.x);
+    u.y = site_sum(wr[1], xm.z, wr[0], xm.x, dd[1], xd.y, du[1], xu.y);
+    u.z = site_sum(wr[2], xm.w, wr[1], xm.y, dd[2], xd.z, du[2], xu.z);
+    u.w = site_sum(wr[3], xr, wr[2], xm.z, dd[3], xd.w, du[3], xu.w);
+    return u;
+}
+
+// block sum of the fused H monitor's three lattice terms into hpart[block][4]
+// (x^4, x^2, x u; no field on a lattice), warps and threads in a fixed order
+__device__ __forceinline__ void torus_ham_block(const HamSum<float> (&hs)[3], double *__restrict__ hpart) {
+    __shared__ double red[kThreads / 32][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        double v = hs[m].value();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) red[warp][m] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        if (threadIdx.x < 3)
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+        hpart[static_cast<int64_t>(blockIdx.x) * 4 + threadIdx.x] = t;
+    }
+}
+
+// 40 registers: 6 CTAs (1536 threads) per SM keep enough loads in flight.
+// TRACE: also the terms of H(x_in) (Eq. Hamilton) for the fused monitor, from
+// the same u = J x_in (same results for x_out).
+template <bool TRACE>
+__global__ void __launch_bounds__(kThreads, TRACE ? 4 : 6)
 torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
                   const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
-                  int tiles, int bpt, float alpha, float zscale, float xscale) {
+                  int tiles, int bpt, float alpha, float zscale, float xscale, double *__restrict__ hpart) {
     const int tile = blockIdx.x % tiles;
     const int part = blockIdx.x / tiles;
     const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
     const int r1 = static_cast<int>(static_cast<int64_t>(Lr) * (part + 1) / bpt);
-    if (r0 >= r1) return;  // uniform over the block
+    if (r0 >= r1) {  // uniform over the block
+        if constexpr (TRACE) {
+            const HamSum<float> none[3];
+            torus_ham_block(none, hpart);
+        }
+        return;
+    }
+    HamSum<float> hs[TRACE ? 3 : 1];
 
     const int ncol4 = Lc >> 2;
     const int c4raw = tile * kThreads + threadIdx.x;
@@ -155,8 +198,30 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
 
         float dd[4];
         unpack4_cvt(dm, dd);
-        const float4 out = row4_new(xm, xl, xr, xu, xd, rt, wleft, dd, du, alpha, zscale, xscale);
-        if (active) __stcs(reinterpret_cast<float4 *>(oc + o), out);
+        if constexpr (TRACE) {
+            float wr[4];
+            unpack4_cvt(rt, wr);
+            const float4 u = row4_u(xm, xl, xr, xu, xd, wr, wleft, dd, du);
+            float4 out;
+            out.x = site_new(u.x, xm.x, alpha, zscale, xscale);
+            out.y = site_new(u.y, xm.y, alpha, zscale, xscale);
+            out.z = site_new(u.z, xm.z, alpha, zscale, xscale);
+            out.w = site_new(u.w, xm.w, alpha, zscale, xscale);
+            if (active) {
+                __stcs(reinterpret_cast<float4 *>(oc + o), out);
+                const float xv[4] = {xm.x, xm.y, xm.z, xm.w}, uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float x2 = xv[q] * xv[q];
+                    hs[0].add(x2 * x2);
+                    hs[1].add(x2);
+                    hs[2].add(xv[q] * uv[q]);
+                }
+            }
+        } else {
+            const float4 out = row4_new(xm, xl, xr, xu, xd, rt, wleft, dd, du, alpha, zscale, xscale);
+            if (active) __stcs(reinterpret_cast<float4 *>(oc + o), out);
+        }
 
         xu = xm; xm = xd; hm = hd;
 #pragma unroll
@@ -164,6 +229,7 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
         xd = xn; hd = hn; dm = dn; rt = rn; wl = wn;
         o = on; od = onn;
     }
+    if constexpr (TRACE) torus_ham_block(hs, hpart);
 }
 
 
@@ -312,6 +378,124 @@ torus_f32_r1_vec4_t2(const float *__restrict__ xi, float *__restrict__ xo,
     cp_async_wait<0>();
 }
 
+// Three DOCH steps per pass: x^(k+3) from x^(k), the intermediate iterates of
+// steps k+1 and k+2 held in registers (two rows each). The layout is that of
+// the two-step kernel: a warp owns kSeg column groups (lanes 1..30; lanes 0 and
+// 31 hold the groups on either side, whose three inner columns stay exact for
+// three steps, since a lane holds four columns) and a strip of rows [r0, r1).
+// Iteration i computes level 1 (step k+1) for row r = r0-2+i from x rows
+// r-1..r+1, level 2 for row r-1 from level-1 rows r-2..r, and level 3 for row
+// r-2 from level-2 rows r-3..r-1, written out; x rows r0-3 .. r1+2 are read.
+// The couplings of a row are unpacked once and kept for the three rows of
+// history the levels need. Same helpers as the single step: the pass equals
+// three single steps bit for bit.
+template <int D>
+__global__ void __launch_bounds__(kThreads, 2)
+torus_f32_r1_vec4_t3(const float *__restrict__ xi, float *__restrict__ xo,
+                     const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
+                     int segs, int bpt, float alpha1, float alpha2, float alpha3, float zscale, float xscale) {
+    extern __shared__ __align__(16) unsigned char t3_smem[];
+    T2Ring<D> &ring = *reinterpret_cast<T2Ring<D> *>(t3_smem);
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = blockIdx.x * (kThreads / 32) + (t >> 5);
+    const int seg = warp % segs;
+    const int part = warp / segs;
+    if (part >= bpt) return;  // uniform over the warp; nothing below synchronises the block
+    const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
+    const int r1 = static_cast<int>(static_cast<int64_t>(Lr) * (part + 1) / bpt);
+    if (r0 >= r1) return;  // uniform over the warp
+
+    const int ncol4 = Lc >> 2;
+    const int g = seg * kSeg + lane - 1;
+    const bool writes = lane >= 1 && lane <= kSeg && g < ncol4;
+    const int c = (((g % ncol4) + ncol4) % ncol4) * 4;
+    const int64_t n = static_cast<int64_t>(Lr) * Lc;
+    const float *xc = xi + c;
+    const int8_t *rc = right + c, *dc = down + c;
+    auto wrap_up = [&](int64_t o) { return o == 0 ? n - Lc : o - Lc; };
+    auto wrap_dn = [&](int64_t o) { o += Lc; return o == n ? int64_t(0) : o; };
+    auto issue = [&](unsigned s, int64_t o) {
+        cp_async16(&ring.x[s][t], xc + o);
+        cp_async4(&ring.rw[s][t], rc + o);
+        cp_async4(&ring.dw[s][t], dc + o);
+    };
+
+    // rows r0-3 and r0-2 are read directly; the ring then carries rows r0-1 .. r1+2
+    const int64_t o0 = static_cast<int64_t>(r0) * Lc;
+    const int64_t om = wrap_up(o0), omm = wrap_up(om), ommm = wrap_up(omm);
+    float4 xu = __ldg(reinterpret_cast<const float4 *>(xc + ommm));
+    float4 xm = __ldg(reinterpret_cast<const float4 *>(xc + omm));
+    float d1[4], d2[4] = {0.f, 0.f, 0.f, 0.f}, d3[4] = {0.f, 0.f, 0.f, 0.f};  // down couplings of rows r-1, r-2, r-3
+    unpack4(__ldg(reinterpret_cast<const int *>(dc + ommm)), d1);
+    int dm = __ldg(reinterpret_cast<const int *>(dc + omm));
+    int rt = __ldg(reinterpret_cast<const int *>(rc + omm));
+    const int rows = r1 - r0 + 4;  // ring bundles: rows r0-1 .. r1+2
+    int64_t oi = om;               // offset of the next row to stage
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        if (q < rows) {
+            issue(q, oi);
+            oi = wrap_dn(oi);
+        }
+        cp_async_commit();
+    }
+    int64_t os = o0;  // offset of the next output row (rows r0, r0+1, ...)
+    float4 ya1 = make_float4(0.f, 0.f, 0.f, 0.f), yb1 = ya1, ya2 = ya1, yb2 = ya1;
+    float w1[4] = {0.f, 0.f, 0.f, 0.f}, w2[4] = {0.f, 0.f, 0.f, 0.f};  // right couplings of rows r-1, r-2
+
+    for (int i = 0; i < rows; ++i) {
+        cp_async_wait<D - 1>();
+        const unsigned s = static_cast<unsigned>(i) % D;
+        const float4 xd = ring.x[s][t];
+        const int rt_n = ring.rw[s][t], dm_n = ring.dw[s][t];
+        if (i + D < rows) {
+            issue(s, oi);
+            oi = wrap_dn(oi);
+        }
+        cp_async_commit();
+
+        // ---- level 1: row r
+        float w0[4], d0[4];
+        unpack4(rt, w0);
+        unpack4(dm, d0);
+        const float xl = __shfl_up_sync(kFull, xm.w, 1);
+        const float xr = __shfl_down_sync(kFull, xm.x, 1);
+        const float wl0 = __shfl_up_sync(kFull, w0[3], 1);
+        const float4 y1 = row4_new_w(xm, xl, xr, xu, xd, w0, wl0, d0, d1, alpha1, zscale, xscale);
+
+        // ---- level 2: row r-1 from level-1 rows r-2, r-1, r
+        float4 y2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i >= 2) {
+            const float yl = __shfl_up_sync(kFull, yb1.w, 1);
+            const float yr = __shfl_down_sync(kFull, yb1.x, 1);
+            const float wl1 = __shfl_up_sync(kFull, w1[3], 1);
+            y2 = row4_new_w(yb1, yl, yr, ya1, y1, w1, wl1, d1, d2, alpha2, zscale, xscale);
+        }
+        // ---- level 3: row r-2 from level-2 rows r-3, r-2, r-1, written out
+        if (i >= 4) {
+            const float zl = __shfl_up_sync(kFull, yb2.w, 1);
+            const float zr = __shfl_down_sync(kFull, yb2.x, 1);
+            const float wl2 = __shfl_up_sync(kFull, w2[3], 1);
+            const float4 z = row4_new_w(yb2, zl, zr, ya2, y2, w2, wl2, d2, d3, alpha3, zscale, xscale);
+            if (writes) __stcs(reinterpret_cast<float4 *>(xo + c + os), z);
+            os = wrap_dn(os);
+        }
+
+        // ---- rotate the histories by one row
+        ya1 = yb1; yb1 = y1;
+        ya2 = yb2; yb2 = y2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            w2[q] = w1[q]; w1[q] = w0[q];
+            d3[q] = d2[q]; d2[q] = d1[q]; d1[q] = d0[q];
+        }
+        xu = xm; xm = xd;
+        dm = dm_n; rt = rt_n;
+    }
+    cp_async_wait<0>();
+}
+
 // Any R, float or double, any alignment: one thread per (site, replica).
 template <typename T>
 __global__ void torus_generic(const T *__restrict__ xi, T *__restrict__ xo,
@@ -356,37 +540,81 @@ int t2_blocks_per_sm() {
     return occ;
 }
 
+int t3_blocks_per_sm() {
+    static int occ = 0;
+    if (!occ) {
+        if (cudaFuncSetAttribute(torus_f32_r1_vec4_t3<kT2Depth>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kT2Smem)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, torus_f32_r1_vec4_t3<kT2Depth>, kThreads,
+                                                          kT2Smem) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+    }
+    return occ;
+}
+
 int vec4_blocks_per_sm() {
     static int occ = 0;
     if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, torus_f32_r1_vec4, kThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, torus_f32_r1_vec4<false>, kThreads, 0) !=
                 cudaSuccess || occ < 1)
             occ = 1;
     }
     return occ;
 }
 
+// launch shape of the single-step fast kernel: column tiles of 1024, bpt row strips per tile
+struct Vec4Shape {
+    int tiles = 0;
+    int64_t bpt = 0;
+    int64_t blocks() const { return bpt * tiles; }
+};
+
+Vec4Shape vec4_shape(const ising_context *c) {
+    const int64_t Lr = c->l_rows, ncol4 = c->l_cols / 4;
+    Vec4Shape v;
+    v.tiles = static_cast<int>((ncol4 + kThreads - 1) / kThreads);
+    const int64_t slots = static_cast<int64_t>(c->num_sms) * vec4_blocks_per_sm();
+    v.bpt = slots / v.tiles;
+    if (v.bpt < 1) v.bpt = 1;
+    if (v.bpt > Lr / 4) v.bpt = Lr / 4 > 0 ? Lr / 4 : 1;
+    return v;
+}
+
+bool vec4_ok(const ising_context *c, const float *x_in, const float *x_out, int R) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(x_in) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(x_out) % 16 == 0);
+    return R == 1 && c->l_cols % 4 == 0 && aligned && c->l_rows < (1LL << 31) && c->l_cols < (1LL << 31);
+}
+
 }  // namespace
+
+ising_status_t torus_step_f32_traced(ising_context *c, const float *x_in, float *x_out, int R, float alpha,
+                                     double inv_beta, double alpha_k, double beta, double *H_out, cudaStream_t st) {
+    if (!vec4_ok(c, x_in, x_out, R)) return ISING_ERR_UNSUPPORTED;
+    const Vec4Shape v = vec4_shape(c);
+    DOCH_CHECK(c->partials.ensure(sizeof(double) * 4 * static_cast<size_t>(v.blocks())));
+    const int k = cbrt_prescale_exp(inv_beta);
+    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+    const float xscale = std::ldexp(1.0f, -k);
+    torus_f32_r1_vec4<true><<<static_cast<unsigned>(v.blocks()), kThreads, 0, st>>>(
+        x_in, x_out, c->right, c->down, static_cast<int>(c->l_rows), static_cast<int>(c->l_cols), v.tiles,
+        static_cast<int>(v.bpt), alpha, zscale, xscale, c->partials.as<double>());
+    DOCH_CUDA(cudaGetLastError());
+    return ham_fused_finish_launch(c->partials.as<double>(), static_cast<int>(v.blocks()), 1, alpha_k, beta, H_out, st);
+}
 
 ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *x_out, int R,
                               float alpha, double inv_beta, cudaStream_t st) {
     const int64_t Lr = c->l_rows, Lc = c->l_cols;
-    const bool aligned = (reinterpret_cast<uintptr_t>(x_in) % 16 == 0) &&
-                         (reinterpret_cast<uintptr_t>(x_out) % 16 == 0);
-    if (R == 1 && Lc % 4 == 0 && aligned && Lr < (1LL << 31) && Lc < (1LL << 31)) {
-        const int64_t ncol4 = Lc / 4;
-        const int tiles = static_cast<int>((ncol4 + kThreads - 1) / kThreads);
-        const int64_t slots = static_cast<int64_t>(c->num_sms) * vec4_blocks_per_sm();
-        int64_t bpt = slots / tiles;
-        if (bpt < 1) bpt = 1;
-        if (bpt > Lr / 4) bpt = Lr / 4 > 0 ? Lr / 4 : 1;
-        const int64_t blocks = bpt * tiles;
+    if (vec4_ok(c, x_in, x_out, R)) {
+        const Vec4Shape v = vec4_shape(c);
         const int k = cbrt_prescale_exp(inv_beta);
         const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
         const float xscale = std::ldexp(1.0f, -k);
-        torus_f32_r1_vec4<<<static_cast<unsigned>(blocks), kThreads, 0, st>>>(
-            x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), tiles,
-            static_cast<int>(bpt), alpha, zscale, xscale);
+        torus_f32_r1_vec4<false><<<static_cast<unsigned>(v.blocks()), kThreads, 0, st>>>(
+            x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), v.tiles,
+            static_cast<int>(v.bpt), alpha, zscale, xscale, nullptr);
     } else {
         const int64_t total = Lr * Lc * R;
         int64_t blocks = (total + 255) / 256;
@@ -425,6 +653,28 @@ ising_status_t torus_pair_f32(const ising_context *c, const float *x_in, float *
     torus_f32_r1_vec4_t2<kT2Depth><<<static_cast<unsigned>(blocks), kThreads, kT2Smem, st>>>(
         x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), static_cast<int>(segs),
         static_cast<int>(bpt), alpha1, alpha2, zscale, xscale);
+    DOCH_CUDA(cudaGetLastError());
+    return ISING_OK;
+}
+
+ising_status_t torus_triple_f32(const ising_context *c, const float *x_in, float *x_out, float alpha1, float alpha2,
+                                float alpha3, double inv_beta, cudaStream_t st) {
+    const int64_t Lr = c->l_rows, Lc = c->l_cols;
+    const int64_t ncol4 = Lc / 4;
+    const int64_t segs = (ncol4 + kSeg - 1) / kSeg;
+    const int64_t warp_slots = static_cast<int64_t>(c->num_sms) * t3_blocks_per_sm() * (kThreads / 32);
+    int64_t bpt = warp_slots / segs;
+    if (bpt < 1) bpt = 1;
+    if (bpt > Lr / 6) bpt = Lr / 6 > 0 ? Lr / 6 : 1;
+    const int64_t warps = segs * bpt;
+    const int64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > INT32_MAX || segs > INT32_MAX) return fail(ISING_ERR_UNSUPPORTED, "lattice too large");
+    const int k = cbrt_prescale_exp(inv_beta);
+    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
+    const float xscale = std::ldexp(1.0f, -k);
+    torus_f32_r1_vec4_t3<kT2Depth><<<static_cast<unsigned>(blocks), kThreads, kT2Smem, st>>>(
+        x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), static_cast<int>(segs),
+        static_cast<int>(bpt), alpha1, alpha2, alpha3, zscale, xscale);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

@@ -106,22 +106,24 @@ def test_torus_generic(shape, R, dtype):
 
 
 @pytest.mark.parametrize("shape", [(37, 1028), (16, 2048), (9, 4), (5, 8), (64, 1024), (100, 3000),
-                                   (4, 120), (7, 124), (300, 968)])
-@pytest.mark.parametrize("iters", [2, 3, 8, 41])
-def test_torus_fused_pairs_match_single_steps(shape, iters):
-    """The two-step pass computes every site with the single-step arithmetic:
-    bit-identical iterates, including an odd remainder step and an alpha schedule."""
+                                   (4, 120), (7, 124), (300, 968), (6, 16)])
+@pytest.mark.parametrize("iters", [2, 3, 4, 8, 41])
+def test_torus_fused_passes_match_single_steps(shape, iters, monkeypatch):
+    """The two- and three-step passes compute every site with the single-step arithmetic:
+    bit-identical iterates for at most 2 and 3 steps per pass (remainders of one and two
+    steps included) and an alpha schedule; lattices with fewer than 6 rows take pairs."""
     t = I.torus_pm1(*shape, seed=107)
     x0 = I.x0_uniform(t.n, 1, seed=108)
     alpha, beta = O.alpha_beta(t, eta=1.0, method="wigner")
     sched = alpha * (1.0 + 0.05 * np.sin(np.arange(iters)))
     out = []
-    for flags in (0, N.FLAG_SINGLE_STEP):
+    for flags, per_pass in ((0, "3"), (0, "2"), (N.FLAG_SINGLE_STEP, "3")):
+        monkeypatch.setenv("ISING_LATTICE_PASS", per_pass)
         with Handle(t, flags=flags) as h:
             x = _dev(x0)
             N.ising_iterate(h, x, sched, [beta], iters)
             out.append(x.cpu().numpy())
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[2])
 
 
 def test_torus_host_buffers_match_device():
@@ -479,3 +481,39 @@ def test_batched_resident_variants_agree(eps, monkeypatch):
         for b, g in enumerate(gs):
             ref = O.doch(O.Problem(g, hs[b].astype(np.float32)), x0[off[b]:off[b + 1]], alphas[b], betas[b], iters)
             _close(xg[off[b]:off[b + 1]], ref, TOL32)
+
+
+@pytest.mark.parametrize("kind", ["csr_step", "lattice"])
+def test_fused_hamiltonian_monitor(kind):
+    """The H monitor fused into the step kernel (the default for a trace) against the exact
+    separate FP64 reduction (taken for FP32 iterates under ISING_FLAG_STRICT_MONOTONE) on the
+    same iterates: the fused form sums FP32 terms with compensated FP32 sums per thread, so
+    the two traces agree to ~1e-7 of the terms' scale (asserted: 1e-5 of the largest |H|);
+    the iterates of a traced run are bit-identical to an untraced run's, and both traces
+    match the oracle's H of the same starting point to the FP32 bar."""
+    if kind == "csr_step":
+        J = I.regular_pm1(70000, 3, seed=66)        # too large for shared memory: the step kernel
+        R, method = 8, "wigner"
+    else:
+        J = I.torus_pm1(96, 512, seed=67)
+        R, method = 1, "wigner"
+    alpha, beta = O.alpha_beta(J, eta=1.0, method=method)
+    x0 = I.x0_uniform(J.n, R, seed=68)
+    iters = 12
+    traces, outs = [], []
+    for flags in (0, N.FLAG_STRICT_MONOTONE):
+        with Handle(J, flags=flags) as h:
+            x = _dev(x0)
+            H = np.zeros((iters + 1, 1, R))
+            N.ising_iterate(h, x, [alpha], [beta], iters, H_trace=H)
+            traces.append(H[:, 0, :])
+            outs.append(x.cpu().numpy())
+    with Handle(J) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], iters)
+        plain = x.cpu().numpy()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], plain)
+    fused, exact = traces
+    assert np.all(np.abs(fused - exact) <= 1e-5 * np.abs(exact).max()), np.abs(fused - exact).max()
+    _, Href = O.doch(O.Problem(J), x0, alpha, beta, 1, trace=True)
+    np.testing.assert_allclose(fused[0], Href[0], rtol=1e-5)

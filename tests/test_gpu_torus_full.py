@@ -2,12 +2,13 @@
 lattice with +-1 couplings (seed 2, x0 seed 2, Wigner parameters, eta = 1),
 FP32, R = 1 -- the configuration bench.py times.
 
-At this width the two-step kernel runs 84 column segments with row strips of
-about 240 rows, so its shared-memory row ring wraps many times per strip; the
-smaller lattices of test_gpu_doch.py never reach that regime. Checks:
+At this width the multi-step passes run 84 column segments with row strips of
+hundreds of rows, so their shared-memory row rings wrap many times per strip;
+the smaller lattices of test_gpu_doch.py never reach that regime. Checks:
 
-  * the fused two-step pass is bit-identical to single steps at 2 and 3
-    iterations (3 ends with the odd single step), on the full lattice;
+  * the fused passes are bit-identical to single steps at 2, 3, 4 and 5
+    iterations (one pair; one triple; a triple and a single step; a triple
+    and a pair), on the full lattice;
   * one step against the oracle, element by element in z-space: the cube of
     the device's x^(1) must equal z = (J x + alpha x)/beta of the oracle
     within 40 * 2^-24 of the step's own scale (sum_j |J_ij x_j| + alpha |x_i|)
@@ -32,7 +33,7 @@ import oracle as O
 from paper_2509_01928_gb300 import _native as N
 from paper_2509_01928_gb300 import build as B
 from paper_2509_01928_gb300 import inputs as I
-from lattice_patch import light_cone_patch
+from oracle.lattice import light_cone_patch
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -61,7 +62,7 @@ def _run(t, x0, alpha, beta, iters, flags=0):
         N.ising_destroy(h)
 
 
-@pytest.mark.parametrize("iters", [2, 3])
+@pytest.mark.parametrize("iters", [2, 3, 4, 5])
 def test_full_lattice_fused_equals_single_steps(lattice, iters):
     t, x0, alpha, beta = lattice
     assert np.array_equal(_run(t, x0, alpha, beta, iters), _run(t, x0, alpha, beta, iters, N.FLAG_SINGLE_STEP))

@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_2509_01928_gb300 import inputs as I
-from lattice_patch import light_cone_patch
+from oracle.lattice import light_cone_patch
 
 
 @pytest.mark.parametrize("r0, c0", [(0, 0), (57, 61), (20, 33)])
