@@ -106,7 +106,7 @@ def test_torus_generic(shape, R, dtype):
 
 
 @pytest.mark.parametrize("shape", [(37, 1028), (16, 2048), (9, 4), (5, 8), (64, 1024), (100, 3000),
-                                   (4, 120), (7, 124), (300, 968), (6, 16)])
+                                   (4, 120), (7, 124), (300, 968), (6, 16), (8, 16)])
 @pytest.mark.parametrize("iters", [2, 3, 4, 8, 41])
 def test_torus_fused_passes_match_single_steps(shape, iters, monkeypatch):
     """The two- and three-step passes compute every site with the single-step arithmetic:
