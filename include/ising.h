@@ -33,6 +33,13 @@
  *    streams stay the caller's. The handle also owns its scratch buffers
  *    (ping-pong state, reduction partials, checkpoints).
  *  - Threads: one handle must not be used by two threads at once.
+ *  - Tuning knobs (environment, read when a handle first needs them):
+ *    ISING_LATTICE_PASS = 1, 2 or 3 caps the DOCH steps one pass over a
+ *    TORUS2D lattice computes (default 2; every setting gives the same
+ *    iterates bit for bit). ISING_RESIDENT_VARIANT = <threads>:<copies>
+ *    (512 or 1024 : 1 or 2) fixes the variant of the shared-memory resident
+ *    kernel for batched instances instead of the handle's autotuner (every
+ *    variant gives the same iterates bit for bit).
  */
 #ifndef ISING_DOCH_H
 #define ISING_DOCH_H
