@@ -68,6 +68,15 @@ def test_full_lattice_fused_equals_single_steps(lattice, iters):
     assert np.array_equal(_run(t, x0, alpha, beta, iters), _run(t, x0, alpha, beta, iters, N.FLAG_SINGLE_STEP))
 
 
+@pytest.mark.parametrize("iters", [3, 5])
+def test_full_lattice_three_step_pass_equals_single_steps(lattice, iters, monkeypatch):
+    """The opt-in three-step pass (ISING_LATTICE_PASS=3) on the full lattice: a triple, and a
+    triple followed by a pair, bit-identical to single steps."""
+    t, x0, alpha, beta = lattice
+    monkeypatch.setenv("ISING_LATTICE_PASS", "3")
+    assert np.array_equal(_run(t, x0, alpha, beta, iters), _run(t, x0, alpha, beta, iters, N.FLAG_SINGLE_STEP))
+
+
 def test_full_lattice_one_step_elementwise(lattice):
     t, x0, alpha, beta = lattice
     x1 = _run(t, x0, alpha, beta, 1).astype(np.float64).ravel()

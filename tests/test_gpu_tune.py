@@ -79,6 +79,9 @@ def test_tune_eta_fp32_scores_are_the_probe_energies():
             assert np.array_equal(E, O.energy_int(O.Problem(t), s)[0])  # exact energies of those spins
         assert best[k] == best.min()
         assert a == pytest.approx(ETAS[k] * a1, rel=1e-15)
+        # a host array as the start gives the same table
+        ah, bh, kh, besth, meanh = N.ising_tune_eta(h, x0.copy(), ETAS, 3, a1, b1)
+        assert (ah, bh, kh) == (a, b, k) and np.array_equal(besth, best) and np.array_equal(meanh, mean)
     finally:
         N.ising_destroy(h)
 
