@@ -353,7 +353,9 @@ ISING_API ising_status_t ising_tune_eta(ising_handle_t h, const void *x0, int32_
  * keeping x^(k) only every ckpt_every steps and recomputing each segment.
  *   x0       [n][R] F32 or F64 (CSR, one instance). The forward iterates
  *            (checkpoints and recomputed segments) run in x0's precision; the
- *            adjoint recursion runs in FP32 with FP64 reductions. d x^(k+1)/d x^k
+ *            adjoint recursion runs in FP32; its sums (dL/dalpha, the loss)
+ *            are compensated FP32 per thread for F32 iterates and FP64 across
+ *            threads (FP64 throughout for F64 iterates). d x^(k+1)/d x^k
  *            contains 1/(3 (x^(k+1))^2), so components passing near zero in
  *            the transient make the gradient sensitive to the trajectory: F64
  *            gives gradients within ~1e-6 of the exact adjoint from any start,

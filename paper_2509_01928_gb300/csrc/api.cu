@@ -1619,7 +1619,9 @@ ising_status_t ising_backward(ising_handle_t h, const void *x0, int32_t xtype, i
         if (R / V > 256) return fail(ISING_ERR_UNSUPPORTED, "ising_backward: R / vector width must be <= 256");
         const int64_t rows_per_block = 256 / (R / V);
         int64_t grid64 = (c->n + rows_per_block - 1) / rows_per_block;
-        if (grid64 > 8LL * c->num_sms) grid64 = 8LL * c->num_sms;
+        // one resident wave: each thread pipelines the loads of its rows
+        if (grid64 > static_cast<int64_t>(kAdjointBlocksPerSm) * c->num_sms)
+            grid64 = static_cast<int64_t>(kAdjointBlocksPerSm) * c->num_sms;
         const int grid = static_cast<int>(grid64 < 1 ? 1 : grid64);
         // layout of the handle's checkpoint buffer
         auto al = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };

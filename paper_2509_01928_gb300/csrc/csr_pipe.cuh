@@ -1,0 +1,35 @@
+// Loads of the CSR row pipeline. A thread that owns rows i, i + S, i + 2S, ...
+// keeps the next row's first batch of column / value entries and the entry range
+// of the row after it in flight while the current row's neighbours are gathered,
+// so a row waits for one round of memory latency instead of three
+// (row_ptr -> col -> gather).
+#pragma once
+
+#include <cstdint>
+
+namespace doch {
+
+// entry range [e0, e1) of row i (empty past the last row)
+__device__ __forceinline__ void pipe_row_range(const int64_t *__restrict__ row_ptr, int64_t i, int64_t n,
+                                               int64_t &e0, int64_t &e1) {
+    if (i < n) {
+        e0 = __ldg(row_ptr + i);
+        e1 = __ldg(row_ptr + i + 1);
+    } else {
+        e0 = e1 = 0;
+    }
+}
+
+// the first B entries of [e0, e1): columns and values as AT (0 past the end)
+template <int B, typename AT, typename VT>
+__device__ __forceinline__ void pipe_first_batch(const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                 int64_t e0, int64_t e1, int32_t (&js)[B], AT (&ws)[B]) {
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+        const bool ok = e0 + t < e1;
+        js[t] = ok ? __ldg(col + e0 + t) : 0;
+        ws[t] = ok ? static_cast<AT>(__ldg(val + e0 + t)) : AT(0);
+    }
+}
+
+}  // namespace doch

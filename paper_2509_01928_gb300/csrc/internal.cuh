@@ -331,6 +331,13 @@ void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2);
 // per-block loss partials, stored as w^(N-1) = g^N / (3 (x^N)^2); one adjoint
 // step from w^k and x^k to w^(k-1) (or g^0 when final_step); FP32 -> FP64
 // widening; the fixed-order finish. zeros counts components x^(k) = 0, k >= 1.
+// The adjoint step kernel is compiled for kAdjointBlocksPerSm resident blocks of
+// 256 threads per SM; its grid is one such wave (grid-stride over the rows).
+constexpr int kAdjointBlocksPerSm = 3;
+// The CSR step for short rows (nnz <= kPipeAvgDeg * n) is compiled for
+// kCsrPipeBlocksPerSm resident blocks of 256 threads per SM.
+constexpr int kCsrPipeBlocksPerSm = 3;
+constexpr int kPipeAvgDeg = 8;
 ising_status_t csr_loss_w(const ising_context *c, const void *x, int xtype, float *w, int R, int V, int grid,
                           double *part, unsigned long long *zeros, cudaStream_t st);
 ising_status_t csr_adjoint_step(const ising_context *c, const float *w_in, const void *x_cur, int xtype,

@@ -23,10 +23,20 @@
 // run. The adjoint kernel of step k gathers w^k at the neighbours and forms, for
 // its own rows, g^k and the next step's w^(k-1) = g^k / (3 (x^k)^2): one
 // gather per neighbour; the loss kernel forms w^(N-1) from g^N. dL/dalpha_k and the loss
-// are FP64 per-block partials summed in block order (run-to-run identical).
+// are summed per thread (for FP32 iterates a compensated FP32 sum of exact product
+// splits, since FP64 arithmetic runs at a small fraction of the FP32 rate on this
+// part; FP64 for FP64 iterates), then in FP64 across threads, blocks and launches
+// in a fixed order (run-to-run identical).
 //
 // Thread layout as in the forward CSR kernel: one thread per (row, chunk of
-// V = 4/2/1 replicas), grid-stride over a fixed grid.
+// V = 4/2/1 replicas), grid-stride over a grid of one resident wave. The adjoint
+// step pipelines its loads across the rows of a thread (row i, i + S, i + 2S, ...):
+// while row i's neighbours are gathered, the first batch of column / value
+// entries of row i + S and the row_ptr pair of row i + 2S are in flight, so a
+// row waits for one round of memory latency instead of three (row_ptr -> col ->
+// gather). Entries past a row's first batch follow in batches, in entry order.
+#include "csr_pipe.cuh"
+#include "hamsum.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -92,8 +102,9 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;
 }
 
-// g^N = -(J x^N + h) / R and per-block partial sums of -1/2 x u - h x (FP64); the
-// kernel stores w^(N-1) = g^N / (3 (x^N)^2) (0 where x^N = 0, counted), the
+// g^N = -(J x^N + h) / R and per-block partial sums of -1/2 x u - h x (per thread
+// a compensated FP32 sum of the products for FP32 iterates, FP64 for FP64 ones;
+// FP64 across the block); the kernel stores w^(N-1) = g^N / (3 (x^N)^2) (0 where x^N = 0, counted), the
 // quantity the first adjoint step gathers. The product u is formed in the
 // iterate type XT.
 template <typename XT, typename VT, int V>
@@ -104,6 +115,7 @@ loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__
     const int C = R / V;
     const XT invR = XT(1) / static_cast<XT>(R);
     double acc = 0.0;
+    DotSum32 acc32;
     unsigned nz = 0;
     const int rows_per_block = kBThreads / C;
     const int ch = threadIdx.x % C;
@@ -140,14 +152,19 @@ loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__
         const XT hi = h ? h[i] : XT(0);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            acc += -0.5 * static_cast<double>(xi[q]) * static_cast<double>(u[q]) -
-                   static_cast<double>(hi) * static_cast<double>(xi[q]);
+            if constexpr (sizeof(XT) == 4) {
+                acc32.add(xi[q], -0.5f * u[q]);
+                if (h) acc32.add(xi[q], -hi);
+            } else {
+                acc += -0.5 * xi[q] * u[q] - hi * xi[q];
+            }
             const float gi = static_cast<float>(-(u[q] + hi) * invR);
             nz += xi[q] == XT(0);
             wi[q] = dcbrt_weight(gi, static_cast<float>(xi[q]));
         }
         st<V>(w + i * R + ch * V, wi);
     }
+    if constexpr (sizeof(XT) == 4) acc = acc32.value();
     const double b = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     unsigned tot = nz;
@@ -162,52 +179,68 @@ loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__
 // or g^0 itself when k = 0 (final). One gather per neighbour: w^k was formed once per
 // row by the step before. Iterates of type XT are rounded to FP32 for this arithmetic.
 template <typename XT, typename VT, int V>
-__global__ void __launch_bounds__(kBThreads)
+__global__ void __launch_bounds__(kBThreads, kAdjointBlocksPerSm)
 adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur, float *__restrict__ w_out,
                     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                     const VT *__restrict__ val, int64_t n, int R, float alpha_k, float inv_beta, int final_step,
                     double *__restrict__ part, unsigned long long *__restrict__ zeros) {
     const int C = R / V;
+    // sum of w x: compensated FP32 for FP32 iterates, FP64 for FP64 iterates
     double ga = 0.0;
+    DotSum32 ga32;
     unsigned nz = 0;
     const int rows_per_block = kBThreads / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * rows_per_block + rl; rl < rows_per_block && i < n;
-         i += static_cast<int64_t>(gridDim.x) * rows_per_block) {
-        float acc[V];
+    const int64_t S = static_cast<int64_t>(gridDim.x) * rows_per_block;
+    // threads past the block's last full row take no rows
+    int64_t i = rl < rows_per_block ? static_cast<int64_t>(blockIdx.x) * rows_per_block + rl : n;
+    int64_t e0, e1, f0, f1;  // entry ranges of rows i and i + S
+    int32_t js[kBatchB];
+    float ws[kBatchB];
+    pipe_row_range(row_ptr, i, n, e0, e1);
+    pipe_row_range(row_ptr, i + S, n, f0, f1);
+    pipe_first_batch<kBatchB>(col, val, e0, e1, js, ws);
+    for (; i < n; i += S) {
+        const int cnt = e1 - e0 < kBatchB ? static_cast<int>(e1 - e0) : kBatchB;
+        float wj[kBatchB][V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) acc[q] = 0.f;
-        const int64_t e1 = __ldg(row_ptr + i + 1);
-        // entries in batches (the last one partial): index/value loads, then the gathers, then
-        // the products in entry order
-        for (int64_t e = __ldg(row_ptr + i); e < e1; e += kBatchB) {
-            const int cnt = e1 - e < kBatchB ? static_cast<int>(e1 - e) : kBatchB;
-            int64_t js[kBatchB];
-            float ws[kBatchB];
-#pragma unroll
-            for (int t = 0; t < kBatchB; ++t) {
-                js[t] = t < cnt ? __ldg(col + e + t) : 0;
-                ws[t] = t < cnt ? static_cast<float>(__ldg(val + e + t)) : 0.f;
-            }
-            float wj[kBatchB][V];
-#pragma unroll
-            for (int t = 0; t < kBatchB; ++t)
-                if (t < cnt) ld<V>(w_in + js[t] * R + ch * V, wj[t]);
-#pragma unroll
-            for (int t = 0; t < kBatchB; ++t)
-                if (t < cnt) {
-#pragma unroll
-                    for (int q = 0; q < V; ++q) acc[q] += ws[t] * wj[t][q];
-                }
-        }
-        float wi[V], out[V];
+        for (int t = 0; t < kBatchB; ++t)
+            if (t < cnt) ld<V>(w_in + static_cast<int64_t>(js[t]) * R + ch * V, wj[t]);
+        float wi[V];
         XT xc[V];
         ld<V>(w_in + i * R + ch * V, wi);
         ld<V>(x_cur + i * R + ch * V, xc);
+        // the next row's first batch and the range of the row after it
+        int32_t js2[kBatchB];
+        float ws2[kBatchB];
+        pipe_first_batch<kBatchB>(col, val, f0, f1, js2, ws2);
+        int64_t g0, g1;
+        pipe_row_range(row_ptr, i + 2 * S, n, g0, g1);
+        float acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kBatchB; ++t)
+            if (t < cnt) {
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] += ws[t] * wj[t][q];
+            }
+        // entries past the first batch, in entry order
+#pragma unroll 4
+        for (int64_t e = e0 + kBatchB; e < e1; ++e) {
+            const int64_t j = __ldg(col + e);
+            const float wv = static_cast<float>(__ldg(val + e));
+            float wr[V];
+            ld<V>(w_in + j * R + ch * V, wr);
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += wv * wr[q];
+        }
+        float out[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            ga += static_cast<double>(wi[q]) * static_cast<double>(xc[q]);
+            if constexpr (sizeof(XT) == 4) ga32.add(wi[q], xc[q]);
+            else ga += static_cast<double>(wi[q]) * xc[q];
             const float g = (acc[q] + alpha_k * wi[q]) * inv_beta;
             if (final_step) {
                 out[q] = g;
@@ -217,7 +250,17 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
             }
         }
         st<V>(w_out + i * R + ch * V, out);
+        e0 = f0;
+        e1 = f1;
+        f0 = g0;
+        f1 = g1;
+#pragma unroll
+        for (int t = 0; t < kBatchB; ++t) {
+            js[t] = js2[t];
+            ws[t] = ws2[t];
+        }
     }
+    if constexpr (sizeof(XT) == 4) ga = ga32.value();
     const double b = block_sum(ga);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     unsigned tot = nz;
@@ -226,20 +269,24 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(zeros, static_cast<unsigned long long>(tot));
 }
 
-// grad_alpha[k] = sum_b part[k][b] / beta (block order); loss = sum_b lpart[b] / R
+// grad_alpha[k] = sum_b part[k][b] / beta; loss = sum_b lpart[b] / R. One warp per
+// output (warp k < iters: grad_alpha[k]; warp iters: the loss): lane l sums the
+// blocks b = l, l + 32, ... in order, then a fixed shuffle tree (run-to-run identical).
 __global__ void adjoint_finish(const double *__restrict__ part, int iters, int blocks, double beta,
                                const double *__restrict__ lpart, int lblocks, int R,
                                double *__restrict__ grad_alpha, double *__restrict__ loss) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < iters) {
-        double s = 0.0;
-        for (int b = 0; b < blocks; ++b) s += part[static_cast<int64_t>(k) * blocks + b];
-        grad_alpha[k] = s / beta;
-    }
-    if (k == 0) {
-        double s = 0.0;
-        for (int b = 0; b < lblocks; ++b) s += lpart[b];
-        *loss = s / R;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k > iters) return;  // whole warps only: blockDim.x is a multiple of 32
+    const double *src = k < iters ? part + static_cast<int64_t>(k) * blocks : lpart;
+    const int m = k < iters ? blocks : lblocks;
+    double s = 0.0;
+    for (int b = lane; b < m; b += 32) s += src[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        if (k < iters) grad_alpha[k] = s / beta;
+        else *loss = s / R;
     }
 }
 
@@ -341,10 +388,10 @@ ising_status_t widen_f32_to_f64(const float *a, double *b, int64_t count, int nu
 ising_status_t adjoint_finish_launch(const double *part, int iters, int blocks, double beta,
                                      const double *lpart, int lblocks, int R, double *grad_alpha,
                                      double *loss, cudaStream_t st) {
-    const int threads = 128;
-    const int nb = (iters > 0 ? iters : 1) + threads - 1;
-    adjoint_finish<<<nb / threads, threads, 0, st>>>(part, iters, blocks, beta, lpart, lblocks, R,
-                                                    grad_alpha, loss);
+    const int threads = 128;                                  // 4 warps per block
+    const int warps = iters + 1;                              // one per gradient entry, one for the loss
+    adjoint_finish<<<(warps + 3) / 4, threads, 0, st>>>(part, iters, blocks, beta, lpart, lblocks, R,
+                                                       grad_alpha, loss);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

@@ -7,12 +7,18 @@
 // consecutive replicas of each neighbour x[j][*] (coalesced) and share the
 // row's col/val entries.
 //
+// csr_step_pipe: the same step for short rows (at most kPipeAvgDeg entries per
+// row on average, one instance, no monitor). The grid is one resident wave and a
+// thread's loads are pipelined across its rows (csr_pipe.cuh); the sums are the
+// ones csr_step forms, in the same order.
+//
 // csr_fused: the whole iteration in one launch for instances that fit in
 // shared memory. One CTA per (instance, replica) keeps that replica's
 // iterate in two shared-memory buffers and separates the steps with
 // __syncthreads(); the CSR arrays stream through L1/L2.
 #include <algorithm>
 
+#include "csr_pipe.cuh"
 #include "hamsum.cuh"
 #include "internal.cuh"
 
@@ -164,6 +170,78 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
     }
 }
 
+constexpr int kPipeB = 4;  // entries of a row's first batch, loaded one row ahead
+
+template <typename XT, typename VT, int V>
+__global__ void __launch_bounds__(256, kCsrPipeBlocksPerSm)
+csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
+                     const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
+                     int64_t n, int R, const XT *__restrict__ alpha_tab, int alpha_len, int k,
+                     const XT *__restrict__ beta_tab) {
+    const int C = R / V;
+    const XT a = alpha_tab[alpha_len == 1 ? 0 : k];
+    const XT bb = beta_tab[0];
+    const int rows_per_block = blockDim.x / C;
+    const int ch = threadIdx.x % C;
+    const int rl = threadIdx.x / C;
+    const int64_t S = static_cast<int64_t>(gridDim.x) * rows_per_block;
+    int64_t i = rl < rows_per_block ? static_cast<int64_t>(blockIdx.x) * rows_per_block + rl : n;
+    int64_t e0, e1, f0, f1;  // entry ranges of rows i and i + S
+    int32_t js[kPipeB];
+    XT ws[kPipeB];
+    pipe_row_range(row_ptr, i, n, e0, e1);
+    pipe_row_range(row_ptr, i + S, n, f0, f1);
+    pipe_first_batch<kPipeB>(col, val, e0, e1, js, ws);
+    for (; i < n; i += S) {
+        const int cnt = e1 - e0 < kPipeB ? static_cast<int>(e1 - e0) : kPipeB;
+        XT xv[kPipeB][V];
+#pragma unroll
+        for (int t = 0; t < kPipeB; ++t)
+            if (t < cnt) ldv<XT, V>(xi + static_cast<int64_t>(js[t]) * R + ch * V, xv[t]);
+        XT xs[V];
+        ldv<XT, V>(xi + i * R + ch * V, xs);
+        const XT hi = h ? h[i] : XT(0);
+        // the next row's first batch and the range of the row after it
+        int32_t js2[kPipeB];
+        XT ws2[kPipeB];
+        pipe_first_batch<kPipeB>(col, val, f0, f1, js2, ws2);
+        int64_t g0, g1;
+        pipe_row_range(row_ptr, i + 2 * S, n, g0, g1);
+        XT acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = XT(0);
+#pragma unroll
+        for (int t = 0; t < kPipeB; ++t)
+            if (t < cnt) {
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] += ws[t] * xv[t][q];
+            }
+        // entries past the first batch, in entry order
+#pragma unroll 4
+        for (int64_t e = e0 + kPipeB; e < e1; ++e) {
+            const int64_t j = __ldg(col + e);
+            const XT w = static_cast<XT>(__ldg(val + e));
+            XT xr[V];
+            ldv<XT, V>(xi + j * R + ch * V, xr);
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += w * xr[q];
+        }
+        XT out[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) out[q] = dcbrt(scale_beta(acc[q] + a * xs[q] + hi, bb));
+        stv<XT, V>(xo + i * R + ch * V, out);
+        e0 = f0;
+        e1 = f1;
+        f0 = g0;
+        f1 = g1;
+#pragma unroll
+        for (int t = 0; t < kPipeB; ++t) {
+            js[t] = js2[t];
+            ws[t] = ws2[t];
+        }
+    }
+}
+
 // One CTA per (instance b = blockIdx.y, replica r = blockIdx.x); shared
 // memory holds two copies of that instance's iterate for replica r.
 template <typename XT, typename VT>
@@ -279,10 +357,30 @@ int step_blocks(const ising_context *c, int C) {
     return static_cast<int>(blocks);
 }
 
+// short rows: the pipelined kernel (one resident wave) serves one instance without the monitor
+bool use_pipe(const ising_context *c, int C, bool traced) {
+    return !traced && c->n_inst == 1 && C <= 256 && c->nnz <= static_cast<int64_t>(kPipeAvgDeg) * c->n;
+}
+
+int pipe_blocks(const ising_context *c, int C) {
+    const int rows_per_block = 256 / C;
+    int64_t blocks = (c->n + rows_per_block - 1) / rows_per_block;
+    const int64_t cap = static_cast<int64_t>(c->num_sms) * kCsrPipeBlocksPerSm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return static_cast<int>(blocks);
+}
+
 template <typename XT, typename VT, int V>
 void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
                  const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, double *hpart, cudaStream_t st) {
     const int C = R / V;
+    if (use_pipe(c, C, hpart != nullptr)) {
+        csr_step_pipe_kernel<XT, VT, V><<<static_cast<unsigned>(pipe_blocks(c, C)), 256, 0, st>>>(
+            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->n, R, alpha_tab, alpha_len, k,
+            beta_tab);
+        return;
+    }
     const int blocks = step_blocks(c, C);
     const int threads = C <= 256 ? 256 : ((C + 31) / 32) * 32;
     if (hpart)

@@ -29,6 +29,7 @@ from paper_2509_01928_gb300 import _native as N
 from paper_2509_01928_gb300 import build as B
 from paper_2509_01928_gb300 import inputs as I
 from fp32_bounds import close32_conditioned, fp32_drift
+from short_rows import short_rows_mixed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -188,6 +189,35 @@ def test_csr_fp32_large_uses_step_kernel():
         x = _dev(x0)
         N.ising_iterate(h, x, [alpha], [beta], 12)
         _close32_conditioned(x.cpu().numpy(), ref, drift)
+
+
+@pytest.mark.parametrize("R,dtype", [(64, np.float32), (6, np.float32), (1, np.float32), (2, np.float64),
+                                     (3, np.float64)])
+def test_csr_short_rows_pipelined_step(R, dtype):
+    """The CSR step for short rows (loads pipelined across a thread's rows, one resident wave)
+    on 40,010 spins, too many for shared memory: empty rows, hub rows longer than the first
+    batch and a hub as the last row. Its iterates are bit-identical to the row-at-a-time step
+    kernel's (the kernel a traced run uses, same sums in the same order) and match the oracle."""
+    g = short_rows_mixed(40010, seed=71)
+    deg = np.diff(g.row_ptr)
+    assert deg.min() == 0 and deg.max() > 4 and deg[-1] > 4 and g.nnz <= 8 * g.n
+    x0 = I.x0_uniform(g.n, R, seed=72, dtype=dtype)
+    alpha, beta = O.alpha_beta(g, eta=1.0, method="wigner")
+    iters = 10
+    with Handle(g) as h:
+        x = _dev(x0)
+        N.ising_iterate(h, x, [alpha], [beta], iters)
+        plain = x.cpu().numpy()
+        x = _dev(x0)
+        H = np.zeros((iters + 1, 1, R))
+        N.ising_iterate(h, x, [alpha], [beta], iters, H_trace=H)
+        traced = x.cpu().numpy()
+    assert np.array_equal(plain, traced)
+    if dtype == np.float64:
+        _close(plain, O.doch(O.Problem(g), x0, alpha, beta, iters), TOL64)
+    else:
+        ref, drift = _fp32_drift(O.Problem(g), x0, alpha, beta, iters)
+        _close32_conditioned(plain, ref, drift)
 
 
 def test_csr_alpha_schedule():
