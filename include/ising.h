@@ -278,7 +278,8 @@ ISING_API ising_status_t ising_iterate_adoch(ising_handle_t h, void *x, int32_t 
 /*
  * DOCH (Algorithm 1) with the stopping rule of Remark S2, per (instance,
  * replica) pair: after each step, r^(k) = ||x^(k+1) - x^(k)||_2 / ||x^(k)||_2
- * (FP64 reduction on the device); the pair stops at the first k with
+ * (compensated FP32 per thread for F32 iterates, FP64 across threads and for
+ * F64 iterates); the pair stops at the first k with
  * r^(k) < eps and keeps x^(k+1). Pairs that never meet the rule run
  * max_iters steps.
  *   x      [n][R] F32 or F64 (in place): each pair's last iterate on return.

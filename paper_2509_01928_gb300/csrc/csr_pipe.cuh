@@ -24,11 +24,13 @@ __device__ __forceinline__ void pipe_row_range(const int64_t *__restrict__ row_p
 template <int B, typename AT, typename VT>
 __device__ __forceinline__ void pipe_first_batch(const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                  int64_t e0, int64_t e1, int32_t (&js)[B], AT (&ws)[B]) {
+    const int m = e1 - e0 < B ? static_cast<int>(e1 - e0) : B;
+    const int32_t *c = col + e0;
+    const VT *v = val + e0;
 #pragma unroll
     for (int t = 0; t < B; ++t) {
-        const bool ok = e0 + t < e1;
-        js[t] = ok ? __ldg(col + e0 + t) : 0;
-        ws[t] = ok ? static_cast<AT>(__ldg(val + e0 + t)) : AT(0);
+        js[t] = t < m ? __ldg(c + t) : 0;
+        ws[t] = t < m ? static_cast<AT>(__ldg(v + t)) : AT(0);
     }
 }
 

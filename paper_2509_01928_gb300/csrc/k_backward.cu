@@ -23,10 +23,12 @@
 // run. The adjoint kernel of step k gathers w^k at the neighbours and forms, for
 // its own rows, g^k and the next step's w^(k-1) = g^k / (3 (x^k)^2): one
 // gather per neighbour; the loss kernel forms w^(N-1) from g^N. dL/dalpha_k and the loss
-// are summed per thread (for FP32 iterates a compensated FP32 sum of exact product
-// splits, since FP64 arithmetic runs at a small fraction of the FP32 rate on this
-// part; FP64 for FP64 iterates), then in FP64 across threads, blocks and launches
-// in a fixed order (run-to-run identical).
+// are summed per thread (for FP32 iterates a compensated FP32 sum: of the row's
+// FP32 dot product in the adjoint step, of exact product splits in the loss;
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this part; FP64
+// for FP64 iterates), then in FP64 across threads, blocks and launches in a
+// fixed order (run-to-run identical). The weights 1 / (3 x^2) use the fast
+// division (within 2 ulp) where the denominator is a normal number.
 //
 // Thread layout as in the forward CSR kernel: one thread per (row, chunk of
 // V = 4/2/1 replicas), grid-stride over a grid of one resident wave. The adjoint
@@ -34,7 +36,7 @@
 // while row i's neighbours are gathered, the first batch of column / value
 // entries of row i + S and the row_ptr pair of row i + 2S are in flight, so a
 // row waits for one round of memory latency instead of three (row_ptr -> col ->
-// gather). Entries past a row's first batch follow in batches, in entry order.
+// gather). Entries past a row's first batch follow one at a time, in entry order.
 #include "csr_pipe.cuh"
 #include "hamsum.cuh"
 #include "internal.cuh"
@@ -84,8 +86,12 @@ __device__ __forceinline__ void st(float *p, const float (&v)[V]) {
     *reinterpret_cast<T *>(p) = w;
 }
 
+// w = g / (3 x^2), 0 where x = 0: the fast division (within 2 ulp) for a normal
+// denominator below 2^126, the IEEE division for the rest
 __device__ __forceinline__ float dcbrt_weight(float g, float x) {
-    return x == 0.0f ? 0.0f : g / (3.0f * x * x);
+    const float d = 3.0f * x * x;
+    if (d >= 0x1p-126f && d < 0x1p126f) return __fdividef(g, d);
+    return x == 0.0f ? 0.0f : g / d;
 }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -237,10 +243,15 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
             for (int q = 0; q < V; ++q) acc[q] += wv * wr[q];
         }
         float out[V];
+        if constexpr (sizeof(XT) == 4) {  // the row's V products in FP32, then the compensated sum
+            float dot = wi[0] * xc[0];
+#pragma unroll
+            for (int q = 1; q < V; ++q) dot = fmaf(wi[q], xc[q], dot);
+            ga32.add(dot);
+        }
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            if constexpr (sizeof(XT) == 4) ga32.add(wi[q], xc[q]);
-            else ga += static_cast<double>(wi[q]) * xc[q];
+            if constexpr (sizeof(XT) == 8) ga += static_cast<double>(wi[q]) * xc[q];
             const float g = (acc[q] + alpha_k * wi[q]) * inv_beta;
             if (final_step) {
                 out[q] = g;

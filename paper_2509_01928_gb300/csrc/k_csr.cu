@@ -5,7 +5,9 @@
 // csr_step: one launch per step. A thread owns one row and a vector chunk of
 // V replicas (V = 4/2/1 floats or 2/1 doubles), so the threads of a row read
 // consecutive replicas of each neighbour x[j][*] (coalesced) and share the
-// row's col/val entries.
+// row's col/val entries. FP32 steps take the cube root as the prescaled
+// power-of-two form of cbrt.cuh (the lattice, batched and dense kernels use the
+// same form), FP64 steps cbrt.
 //
 // csr_step_pipe: the same step for short rows (at most kPipeAvgDeg entries per
 // row on average, one instance, no monitor). The grid is one resident wave and a
@@ -18,6 +20,7 @@
 // __syncthreads(); the CSR arrays stream through L1/L2.
 #include <algorithm>
 
+#include "cbrt.cuh"
 #include "csr_pipe.cuh"
 #include "hamsum.cuh"
 #include "internal.cuh"
@@ -31,11 +34,13 @@ __device__ __forceinline__ T dcbrt(T z) {
     else return cbrt(z);
 }
 
-// scale by 1/beta: float tables hold 1/beta (multiply), double tables hold beta (divide)
+// The update of the step kernels, x = cbrt(z / beta) for z = (J x + alpha x + h)_i:
+// FP32 through the prescaled power-of-two cube root (cbrt.cuh; zs = 2^(3k) / beta,
+// xsc = 2^-k per instance), FP64 through cbrt(z / beta).
 template <typename T>
-__device__ __forceinline__ T scale_beta(T v, T b) {
-    if constexpr (sizeof(T) == 4) return v * b;
-    else return v / b;
+__device__ __forceinline__ T step_update(T z, T beta, float zs, float xsc) {
+    if constexpr (sizeof(T) == 4) return cbrt_pow2(z * zs) * xsc;
+    else return cbrt(z / beta);
 }
 
 __device__ __forceinline__ int find_inst(const int64_t *__restrict__ off, int n_inst, int64_t i) {
@@ -87,7 +92,8 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
                 const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
                 const int64_t *__restrict__ inst_off, int n_inst, int64_t n, int R,
                 const XT *__restrict__ alpha_tab, int alpha_len, int k,
-                const XT *__restrict__ beta_tab, double *__restrict__ hpart) {
+                const XT *__restrict__ beta_tab, const float *__restrict__ zs_tab,
+                const float *__restrict__ xs_tab, double *__restrict__ hpart) {
     const int C = R / V;
     const int ak = alpha_len == 1 ? 0 : k;
     // each thread keeps one replica chunk and strides over rows: no division in the loop
@@ -100,6 +106,11 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
         const int b = n_inst > 1 ? find_inst(inst_off, n_inst, i) : 0;
         const XT a = alpha_tab[static_cast<int64_t>(b) * alpha_len + ak];
         const XT bb = beta_tab[b];
+        float zs = 1.f, xsc = 1.f;
+        if constexpr (sizeof(XT) == 4) {
+            zs = __ldg(zs_tab + b);
+            xsc = __ldg(xs_tab + b);
+        }
         XT acc[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) acc[q] = XT(0);
@@ -135,7 +146,7 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
         ldv<XT, V>(xi + i * R + ch * V, xs);
         const XT hi = h ? h[i] : XT(0);
 #pragma unroll
-        for (int q = 0; q < V; ++q) out[q] = dcbrt(scale_beta(acc[q] + a * xs[q] + hi, bb));
+        for (int q = 0; q < V; ++q) out[q] = step_update(acc[q] + a * xs[q] + hi, bb, zs, xsc);
         stv<XT, V>(xo + i * R + ch * V, out);
         if constexpr (TRACE) {
 #pragma unroll
@@ -177,10 +188,16 @@ __global__ void __launch_bounds__(256, kCsrPipeBlocksPerSm)
 csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
                      const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
                      int64_t n, int R, const XT *__restrict__ alpha_tab, int alpha_len, int k,
-                     const XT *__restrict__ beta_tab) {
+                     const XT *__restrict__ beta_tab, const float *__restrict__ zs_tab,
+                     const float *__restrict__ xs_tab) {
     const int C = R / V;
     const XT a = alpha_tab[alpha_len == 1 ? 0 : k];
     const XT bb = beta_tab[0];
+    float zs = 1.f, xsc = 1.f;
+    if constexpr (sizeof(XT) == 4) {
+        zs = zs_tab[0];
+        xsc = xs_tab[0];
+    }
     const int rows_per_block = blockDim.x / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
@@ -228,7 +245,7 @@ csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64
         }
         XT out[V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) out[q] = dcbrt(scale_beta(acc[q] + a * xs[q] + hi, bb));
+        for (int q = 0; q < V; ++q) out[q] = step_update(acc[q] + a * xs[q] + hi, bb, zs, xsc);
         stv<XT, V>(xo + i * R + ch * V, out);
         e0 = f0;
         e1 = f1;
@@ -371,14 +388,24 @@ int pipe_blocks(const ising_context *c, int C) {
     return static_cast<int>(blocks);
 }
 
+// the update tables of a step: beta (FP64) or the cube root's prescale (FP32, per instance)
+template <typename XT>
+struct StepTabs {
+    const XT *alpha;
+    int alpha_len;
+    const XT *beta;
+    const float *zs;
+    const float *xsc;
+};
+
 template <typename XT, typename VT, int V>
-void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
-                 const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, double *hpart, cudaStream_t st) {
+void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h, const StepTabs<XT> &t, int k,
+                 double *hpart, cudaStream_t st) {
     const int C = R / V;
     if (use_pipe(c, C, hpart != nullptr)) {
         csr_step_pipe_kernel<XT, VT, V><<<static_cast<unsigned>(pipe_blocks(c, C)), 256, 0, st>>>(
-            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->n, R, alpha_tab, alpha_len, k,
-            beta_tab);
+            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->n, R, t.alpha, t.alpha_len, k,
+            t.beta, t.zs, t.xsc);
         return;
     }
     const int blocks = step_blocks(c, C);
@@ -386,24 +413,23 @@ void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *
     if (hpart)
         csr_step_kernel<XT, VT, V, true><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
             xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
-            c->n, R, alpha_tab, alpha_len, k, beta_tab, hpart);
+            c->n, R, t.alpha, t.alpha_len, k, t.beta, t.zs, t.xsc, hpart);
     else
         csr_step_kernel<XT, VT, V, false><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
             xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->inst_off, c->n_inst,
-            c->n, R, alpha_tab, alpha_len, k, beta_tab, nullptr);
+            c->n, R, t.alpha, t.alpha_len, k, t.beta, t.zs, t.xsc, nullptr);
 }
 
 template <typename XT, int V>
-ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h,
-                            const XT *alpha_tab, int alpha_len, int k, const XT *beta_tab, double *hpart,
-                            cudaStream_t st) {
+ising_status_t dispatch_val(const ising_context *c, const XT *xi, XT *xo, int R, const XT *h, const StepTabs<XT> &t,
+                            int k, double *hpart, cudaStream_t st) {
     if (R / V > 1024) return fail(ISING_ERR_UNSUPPORTED, "CSR step: R / vector width must be <= 1024");
     if (hpart && R / V > 256) return ISING_ERR_UNSUPPORTED;  // the fused monitor needs one row per 256 threads
     switch (c->jtype) {
-        case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
-        case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
-        case ISING_F32: launch_step<XT, float, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
-        case ISING_F64: launch_step<XT, double, V>(c, xi, xo, R, h, alpha_tab, alpha_len, k, beta_tab, hpart, st); break;
+        case ISING_I8: launch_step<XT, int8_t, V>(c, xi, xo, R, h, t, k, hpart, st); break;
+        case ISING_I32: launch_step<XT, int32_t, V>(c, xi, xo, R, h, t, k, hpart, st); break;
+        case ISING_F32: launch_step<XT, float, V>(c, xi, xo, R, h, t, k, hpart, st); break;
+        case ISING_F64: launch_step<XT, double, V>(c, xi, xo, R, h, t, k, hpart, st); break;
         default: return fail(ISING_ERR_UNSUPPORTED, "CSR value type not supported on the device");
     }
     DOCH_CUDA(cudaGetLastError());
@@ -507,30 +533,28 @@ static ising_status_t csr_step_impl(const ising_context *c, const void *xi, void
     if (xtype == ISING_F32) {
         const float *x_in = static_cast<const float *>(xi);
         float *x_out = static_cast<float *>(xo);
+        const StepTabs<float> t{p.alpha_f, p.alpha_len, p.inv_beta_f, p.zscale_f, p.xscale_f};
         if (R % 4 == 0 && a % 16 == 0) {
             *blocks = step_blocks(c, R / 4);
-            return dispatch_val<float, 4>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f,
-                                          hpart, st);
+            return dispatch_val<float, 4>(c, x_in, x_out, R, c->h_f32, t, k, hpart, st);
         }
         if (R % 2 == 0 && a % 8 == 0) {
             *blocks = step_blocks(c, R / 2);
-            return dispatch_val<float, 2>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f,
-                                          hpart, st);
+            return dispatch_val<float, 2>(c, x_in, x_out, R, c->h_f32, t, k, hpart, st);
         }
         *blocks = step_blocks(c, R);
-        return dispatch_val<float, 1>(c, x_in, x_out, R, c->h_f32, p.alpha_f, p.alpha_len, k, p.inv_beta_f, hpart,
-                                      st);
+        return dispatch_val<float, 1>(c, x_in, x_out, R, c->h_f32, t, k, hpart, st);
     }
     if (xtype == ISING_F64) {
         const double *x_in = static_cast<const double *>(xi);
         double *x_out = static_cast<double *>(xo);
+        const StepTabs<double> t{p.alpha_d, p.alpha_len, p.beta_d, nullptr, nullptr};
         if (R % 2 == 0 && a % 16 == 0) {
             *blocks = step_blocks(c, R / 2);
-            return dispatch_val<double, 2>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, hpart,
-                                           st);
+            return dispatch_val<double, 2>(c, x_in, x_out, R, c->h_f64, t, k, hpart, st);
         }
         *blocks = step_blocks(c, R);
-        return dispatch_val<double, 1>(c, x_in, x_out, R, c->h_f64, p.alpha_d, p.alpha_len, k, p.beta_d, hpart, st);
+        return dispatch_val<double, 1>(c, x_in, x_out, R, c->h_f64, t, k, hpart, st);
     }
     return fail(ISING_ERR_UNSUPPORTED, "CSR iterate type must be F32 or F64");
 }

@@ -1,8 +1,11 @@
 // Stopping rule of Remark S2 per (instance, replica) pair: after the step
 // x^(k) -> x^(k+1), r^(k) = ||x^(k+1) - x^(k)||_2 / ||x^(k)||_2, and a pair
 // stops at the first k with r^(k) < eps, keeping x^(k+1).
-//  norm pass: per (instance, replica, chunk) block, FP64 partial sums of
-//             (x^(k+1) - x^(k))^2 and (x^(k))^2 in a fixed order;
+//  norm pass: per (instance, replica, chunk) block, partial sums of
+//             (x^(k+1) - x^(k))^2 and (x^(k))^2 in a fixed order: per thread a
+//             compensated FP32 sum for FP32 iterates (FP64 arithmetic runs at a
+//             small fraction of the FP32 rate on this part), FP64 for FP64
+//             iterates; FP64 across threads;
 //  decide:    one block per pair adds the chunk partials in a fixed order,
 //             evaluates r^(k) and, for a pair still running, records the step
 //             count, marks it stopped and lowers the running-pair counter;
@@ -10,6 +13,7 @@
 //             result; pairs that never stop take x^(max_iters) at the end.
 #include <cmath>
 
+#include "hamsum.cuh"
 #include "internal.cuh"
 
 namespace doch {
@@ -28,11 +32,23 @@ stop_norms(const XT *__restrict__ xc, const XT *__restrict__ xn, const int64_t *
     const int64_t len = hi - lo;
     const int64_t s0 = lo + len * ch / chunks, s1 = lo + len * (ch + 1) / chunks;
     double d = 0.0, s = 0.0;
+    DotSum32 d32, s32;
     for (int64_t i = s0 + threadIdx.x; i < s1; i += kSThreads) {
-        const double a = static_cast<double>(xc[i * R + r]);
-        const double e = static_cast<double>(xn[i * R + r]) - a;
-        d += e * e;
-        s += a * a;
+        if constexpr (sizeof(XT) == 4) {
+            const float a = xc[i * R + r];
+            const float e = xn[i * R + r] - a;
+            d32.add(e, e);
+            s32.add(a, a);
+        } else {
+            const double a = xc[i * R + r];
+            const double e = xn[i * R + r] - a;
+            d += e * e;
+            s += a * a;
+        }
+    }
+    if constexpr (sizeof(XT) == 4) {
+        d = d32.value();
+        s = s32.value();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

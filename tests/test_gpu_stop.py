@@ -1,8 +1,8 @@
 """The stopping rule of Remark S2 on the device against the FP64 oracle.
 
 A pair's step count is an integer decided by floating point: r^(k) < eps.
-The device reduces r^(k) in FP64 in another order than the oracle (and from
-FP32 iterates on the FP32 path), so the counts are compared where the
+The device reduces r^(k) in another order than the oracle (FP64; compensated
+FP32 per thread from FP32 iterates on the FP32 path), so the counts are compared where the
 oracle's r^(k) stays clear of eps up to its stopping step (relative margin
 1e-9 in FP64, 1e-3 in FP32); where the counts agree the iterates are compared
 at the parity tolerance of the path (FP64 1e-10, FP32 1e-5).
