@@ -506,13 +506,18 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
         DOCH_CHECK(upload(&c->row_ptr, hp.row_ptr.data(), sizeof(int64_t) * hp.row_ptr.size()));
         DOCH_CHECK(upload(&c->col, hp.col.data(), sizeof(int32_t) * hp.col.size()));
         if (hp.n_inst > 1 && c->max_inst_n <= 65536) {
-            // transposed ELL copy for the shared-memory resident batched kernel
+            // transposed ELL copy for the shared-memory resident batched kernel, in slot
+            // pairs: slots 2p and 2p + 1 of row i sit side by side at pair p, row i
+            // ([pair][row][2]), so one 4-byte load gives a row two columns and one 8-byte
+            // load two weights. Slots past a row's entries (and the one that makes the
+            // width even) hold the row itself with weight 0.
             std::vector<int64_t> eoff(hp.n_inst + 1, 0);
             c->ell_deg_h.assign(hp.n_inst, 0);
             for (int b = 0; b < hp.n_inst; ++b) {
                 int d = 0;
                 for (int64_t i = hp.off[b]; i < hp.off[b + 1]; ++i)
                     d = std::max<int>(d, static_cast<int>(hp.row_ptr[i + 1] - hp.row_ptr[i]));
+                d += d & 1;
                 c->ell_deg_h[b] = d;
                 eoff[b + 1] = eoff[b] + static_cast<int64_t>(d) * (hp.off[b + 1] - hp.off[b]);
             }
@@ -523,7 +528,7 @@ ising_status_t build_context(const HostProblem &hp, int flags, ising_context *c)
                 for (int64_t i = 0; i < nb; ++i) {
                     const int64_t e0 = hp.row_ptr[lo + i], cnt = hp.row_ptr[lo + i + 1] - e0;
                     for (int k = 0; k < c->ell_deg_h[b]; ++k) {
-                        const size_t at = static_cast<size_t>(eoff[b] + k * nb + i);
+                        const size_t at = static_cast<size_t>(eoff[b] + ((k >> 1) * nb + i) * 2 + (k & 1));
                         ec[at] = static_cast<uint16_t>(k < cnt ? hp.col[e0 + k] - lo : i);
                         ev[at] = k < cnt ? static_cast<float>(hp.val[e0 + k]) : 0.f;
                     }

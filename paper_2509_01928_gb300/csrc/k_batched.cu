@@ -24,6 +24,7 @@ namespace doch {
 namespace {
 
 constexpr int kBatch = 8;  // neighbours whose loads are issued together
+constexpr int kPairBatch = 4;  // ELL slot pairs whose loads are issued together (resident kernel)
 
 template <int V> struct FV;
 template <> struct FV<1> { using type = float; };
@@ -157,8 +158,10 @@ ising_status_t dispatch_b(const ising_context *c, const BatchedConfig &cfg, floa
 // g0+G-1); one CTA runs all steps of an item with both Jacobi copies of that
 // slice of the iterate in shared memory ([n_b][G] floats each), so every
 // neighbour gather is a G-wide shared-memory load and only the couplings are
-// re-read (from L2) each step, from the transposed ELL copy: slot k of rows
-// i .. i+31 is 32 consecutive entries, one coalesced load per warp. G is chosen per instance, the largest power of
+// re-read (from L2) each step, from the transposed ELL copy in slot pairs:
+// pair p of rows i .. i+31 is 32 consecutive (column, column) and (weight,
+// weight) pairs, one coalesced 4-byte and one 8-byte load per warp for two
+// slots (the width D is even). G is chosen per instance, the largest power of
 // two dividing R with 2 n_b G floats fitting the CTA's shared memory. Items
 // are queued longest first; the iterate is updated in place in global memory
 // at the end of the item (items own disjoint slices).
@@ -192,6 +195,44 @@ __device__ __forceinline__ void st_vec(float *p, const float (&v)[G]) {
     }
 }
 
+// Row j of an iterate slice in shared memory ([n_b][G] floats). For G >= 8 the
+// 16-byte chunks of a row are permuted by an XOR of bits of j, so that the chunk c
+// of random rows spreads over all eight 16-byte bank groups of a 128-byte line
+// (without it, rows of 32 or 64 bytes put chunk c in only 4 or 2 of them, and the
+// random neighbour gathers of a warp conflict 2-4 times as often).
+template <int G>
+__device__ __forceinline__ int swz(int j, int c) {
+    if constexpr (G == 16) return c ^ ((j >> 1) & 3);
+    else if constexpr (G == 8) return c ^ ((j >> 2) & 1);
+    else return c;
+}
+
+template <int G>
+__device__ __forceinline__ void lds_row(const float *base, int j, float (&v)[G]) {
+    if constexpr (G >= 8) {
+        const float4 *r = reinterpret_cast<const float4 *>(base + j * G);
+#pragma unroll
+        for (int c = 0; c < G / 4; ++c) {
+            const float4 t = r[swz<G>(j, c)];
+            v[4 * c] = t.x; v[4 * c + 1] = t.y; v[4 * c + 2] = t.z; v[4 * c + 3] = t.w;
+        }
+    } else {
+        ldg_vec<G>(base + j * G, v);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void sts_row(float *base, int j, const float (&v)[G]) {
+    if constexpr (G >= 8) {
+        float4 *r = reinterpret_cast<float4 *>(base + j * G);
+#pragma unroll
+        for (int c = 0; c < G / 4; ++c)
+            r[swz<G>(j, c)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    } else {
+        st_vec<G>(base + j * G, v);
+    }
+}
+
 // Stopping rule of Remark S2 inside the resident kernel (eps > 0): block-wide
 // sums of (x^(k+1) - x^(k))^2 and (x^(k))^2 per replica of the item (FP32 per
 // thread and warp, FP64 across warps); a replica with r^(k) < eps is frozen
@@ -217,10 +258,14 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
                                               float *gx, int pair0, const ResidentStop &stop) {
     const int T = blockDim.x;
     constexpr bool stopping = STOP;
+    // the slot pairs: (column 2p | column 2p + 1 << 16) and (weight 2p, weight 2p + 1);
+    // ecol and eval start at an even slot (the widths are even), so these are aligned
+    const uint32_t *__restrict__ ecol2 = reinterpret_cast<const uint32_t *>(ecol);
+    const float2 *__restrict__ eval2 = reinterpret_cast<const float2 *>(eval);
     for (int i = threadIdx.x; i < nb; i += T) {
         float v[G];
         ldg_vec<G>(x + (lo + i) * R + g0, v);
-        st_vec<G>(s0 + i * G, v);
+        sts_row<G>(s0, i, v);
     }
     if (STOP && threadIdx.x < G) {
         stop.frozen[threadIdx.x] = 0;
@@ -244,29 +289,33 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
             float acc[G];
 #pragma unroll
             for (int q = 0; q < G; ++q) acc[q] = 0.f;
-            // slots in batches of kBatch: the (coalesced) index/weight loads of a batch first,
-            // then the shared-memory gathers and products in CSR order
-            for (int k0 = 0; k0 < D; k0 += kBatch) {
-                const int cnt = D - k0 < kBatch ? D - k0 : kBatch;
-                int js[kBatch];
-                float ws[kBatch];
+            // slot pairs in batches of kPairBatch: the (coalesced) index/weight loads of a
+            // batch first, then the shared-memory gathers and products in CSR order
+            const int D2 = D >> 1;
+            for (int p0 = 0; p0 < D2; p0 += kPairBatch) {
+                const int cnt = D2 - p0 < kPairBatch ? D2 - p0 : kPairBatch;
+                uint32_t jj[kPairBatch];
+                float2 ww[kPairBatch];
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    const int at = (k0 + q) * nb + i;  // < D n_b < 2^31 (checked on the host)
-                    js[q] = q < cnt ? static_cast<int>(__ldg(ecol + at)) : 0;
-                    ws[q] = q < cnt ? __ldg(eval + at) : 0.f;
+                for (int q = 0; q < kPairBatch; ++q) {
+                    const int at = (p0 + q) * nb + i;  // < D n_b / 2 < 2^31 (checked on the host)
+                    jj[q] = q < cnt ? __ldg(ecol2 + at) : 0u;
+                    ww[q] = q < cnt ? __ldg(eval2 + at) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q)
+                for (int q = 0; q < kPairBatch; ++q)
                     if (q < cnt) {
                         float xv[G];
-                        ldg_vec<G>(cur + js[q] * G, xv);
+                        lds_row<G>(cur, static_cast<int>(jj[q] & 0xffffu), xv);
 #pragma unroll
-                        for (int r = 0; r < G; ++r) acc[r] += ws[q] * xv[r];
+                        for (int r = 0; r < G; ++r) acc[r] += ww[q].x * xv[r];
+                        lds_row<G>(cur, static_cast<int>(jj[q] >> 16), xv);
+#pragma unroll
+                        for (int r = 0; r < G; ++r) acc[r] += ww[q].y * xv[r];
                     }
             }
             float xs[G], out[G];
-            ldg_vec<G>(cur + i * G, xs);
+            lds_row<G>(cur, i, xs);
             const float hv = h ? __ldg(h + lo + i) : 0.f;
 #pragma unroll
             for (int q = 0; q < G; ++q) out[q] = cbrt_pow2((acc[q] + a * xs[q] + hv) * zs) * xsc;
@@ -280,7 +329,7 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
                 }
             }
             if constexpr (ONECOPY) st_vec<G>(gx + static_cast<int64_t>(i) * G, out);
-            else st_vec<G>(nxt + i * G, out);
+            else sts_row<G>(nxt, i, out);
         }
         if constexpr (STOP) {
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -324,7 +373,7 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
                 for (int i = threadIdx.x; i < nb; i += T) {
                     float v[G];
                     ldg_vec<G>(gx + static_cast<int64_t>(i) * G, v);
-                    st_vec<G>(cur + i * G, v);
+                    sts_row<G>(cur, i, v);
                 }
                 __syncthreads();
             }
@@ -337,9 +386,9 @@ __device__ __forceinline__ void resident_item(float *__restrict__ x, int R, int6
         float v[G];
         if constexpr (ONECOPY) {
             if (iters > 0) ldg_vec<G>(gx + static_cast<int64_t>(i) * G, v);
-            else ldg_vec<G>(cur + i * G, v);
+            else lds_row<G>(cur, i, v);
         } else {
-            ldg_vec<G>(cur + i * G, v);
+            lds_row<G>(cur, i, v);
         }
         st_vec<G>(x + (lo + i) * R + g0, v);
     }
