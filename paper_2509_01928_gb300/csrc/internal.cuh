@@ -335,8 +335,9 @@ void proc_closed_sums(int64_t n, int64_t c, double *s1, double *s2);
 // 256 threads per SM; its grid is one such wave (grid-stride over the rows).
 constexpr int kAdjointBlocksPerSm = 3;
 // The CSR step for short rows (nnz <= kPipeAvgDeg * n) is compiled for
-// kCsrPipeBlocksPerSm resident blocks of 256 threads per SM.
-constexpr int kCsrPipeBlocksPerSm = 3;
+// kCsrPipeBlocksPerSm resident blocks of 256 threads per SM (FP32 iterates;
+// FP64 iterates, which need more registers: one block fewer).
+constexpr int kCsrPipeBlocksPerSm = 4;
 constexpr int kPipeAvgDeg = 8;
 ising_status_t csr_loss_w(const ising_context *c, const void *x, int xtype, float *w, int R, int V, int grid,
                           double *part, unsigned long long *zeros, cudaStream_t st);

@@ -184,11 +184,11 @@ loss_w_kernel(const XT *__restrict__ x, float *__restrict__ w, const int64_t *__
 // then the next step's w^(k-1)_i = g^k_i / (3 (x^k_i)^2) (0 where x^k_i = 0, counted),
 // or g^0 itself when k = 0 (final). One gather per neighbour: w^k was formed once per
 // row by the step before. Iterates of type XT are rounded to FP32 for this arithmetic.
-template <typename XT, typename VT, int V>
+template <typename XT, typename VT, int V, typename IT>
 __global__ void __launch_bounds__(kBThreads, kAdjointBlocksPerSm)
 adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur, float *__restrict__ w_out,
                     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                    const VT *__restrict__ val, int64_t n, int R, float alpha_k, float inv_beta, int final_step,
+                    const VT *__restrict__ val, IT n, int R, float alpha_k, float inv_beta, int final_step,
                     double *__restrict__ part, unsigned long long *__restrict__ zeros) {
     const int C = R / V;
     // sum of w x: compensated FP32 for FP32 iterates, FP64 for FP64 iterates
@@ -198,10 +198,10 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
     const int rows_per_block = kBThreads / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
-    const int64_t S = static_cast<int64_t>(gridDim.x) * rows_per_block;
+    const IT S = static_cast<IT>(gridDim.x) * rows_per_block;
     // threads past the block's last full row take no rows
-    int64_t i = rl < rows_per_block ? static_cast<int64_t>(blockIdx.x) * rows_per_block + rl : n;
-    int64_t e0, e1, f0, f1;  // entry ranges of rows i and i + S
+    IT i = rl < rows_per_block ? static_cast<IT>(blockIdx.x) * rows_per_block + rl : n;
+    IT e0, e1, f0, f1;  // entry ranges of rows i and i + S
     int32_t js[kBatchB];
     float ws[kBatchB];
     pipe_row_range(row_ptr, i, n, e0, e1);
@@ -215,13 +215,13 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
             if (t < cnt) ld<V>(w_in + static_cast<int64_t>(js[t]) * R + ch * V, wj[t]);
         float wi[V];
         XT xc[V];
-        ld<V>(w_in + i * R + ch * V, wi);
-        ld<V>(x_cur + i * R + ch * V, xc);
+        ld<V>(w_in + static_cast<int64_t>(i) * R + ch * V, wi);
+        ld<V>(x_cur + static_cast<int64_t>(i) * R + ch * V, xc);
         // the next row's first batch and the range of the row after it
         int32_t js2[kBatchB];
         float ws2[kBatchB];
         pipe_first_batch<kBatchB>(col, val, f0, f1, js2, ws2);
-        int64_t g0, g1;
+        IT g0, g1;
         pipe_row_range(row_ptr, i + 2 * S, n, g0, g1);
         float acc[V];
 #pragma unroll
@@ -234,7 +234,7 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
             }
         // entries past the first batch, in entry order
 #pragma unroll 4
-        for (int64_t e = e0 + kBatchB; e < e1; ++e) {
+        for (IT e = e0 + kBatchB; e < e1; ++e) {
             const int64_t j = __ldg(col + e);
             const float wv = static_cast<float>(__ldg(val + e));
             float wr[V];
@@ -260,7 +260,7 @@ adjoint_step_kernel(const float *__restrict__ w_in, const XT *__restrict__ x_cur
                 out[q] = dcbrt_weight(g, static_cast<float>(xc[q]));
             }
         }
-        st<V>(w_out + i * R + ch * V, out);
+        st<V>(w_out + static_cast<int64_t>(i) * R + ch * V, out);
         e0 = f0;
         e1 = f1;
         f0 = g0;
@@ -319,9 +319,14 @@ void launch_loss(const ising_context *c, const XT *x, float *w, int R, int grid,
 template <typename XT, typename VT, int V>
 void launch_adj(const ising_context *c, const float *wi, const XT *xc, float *wo, int R, float a, float ib,
                 int final_step, int grid, double *part, unsigned long long *zeros, cudaStream_t st) {
-    adjoint_step_kernel<XT, VT, V><<<grid, kBThreads, 0, st>>>(wi, xc, wo, c->row_ptr, c->col,
-                                                               static_cast<const VT *>(c->val), c->n, R, a, ib,
-                                                               final_step, part, zeros);
+    if (c->n < (int64_t(1) << 30) && c->nnz < (int64_t(1) << 30))  // 32-bit rows and entry offsets
+        adjoint_step_kernel<XT, VT, V, int><<<grid, kBThreads, 0, st>>>(
+            wi, xc, wo, c->row_ptr, c->col, static_cast<const VT *>(c->val), static_cast<int>(c->n), R, a, ib,
+            final_step, part, zeros);
+    else
+        adjoint_step_kernel<XT, VT, V, int64_t><<<grid, kBThreads, 0, st>>>(
+            wi, xc, wo, c->row_ptr, c->col, static_cast<const VT *>(c->val), c->n, R, a, ib, final_step, part,
+            zeros);
 }
 
 template <typename XT, typename VT>

@@ -190,11 +190,15 @@ csr_step_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *_
 
 constexpr int kPipeB = 4;  // entries of a row's first batch, loaded one row ahead
 
+// Rows and entry offsets are 32-bit here (n, nnz < 2^30, checked by use_pipe).
+template <typename XT>
+constexpr int pipe_blocks_per_sm() { return sizeof(XT) == 4 ? kCsrPipeBlocksPerSm : kCsrPipeBlocksPerSm - 1; }
+
 template <typename XT, typename VT, int V>
-__global__ void __launch_bounds__(256, kCsrPipeBlocksPerSm)
+__global__ void __launch_bounds__(256, pipe_blocks_per_sm<XT>())
 csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64_t *__restrict__ row_ptr,
                      const int32_t *__restrict__ col, const VT *__restrict__ val, const XT *__restrict__ h,
-                     int64_t n, int R, const XT *__restrict__ alpha_tab, int alpha_len, int k,
+                     int n, int R, const XT *__restrict__ alpha_tab, int alpha_len, int k,
                      const XT *__restrict__ beta_tab, const float *__restrict__ zs_tab,
                      const float *__restrict__ xs_tab) {
     const int C = R / V;
@@ -208,9 +212,9 @@ csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64
     const int rows_per_block = blockDim.x / C;
     const int ch = threadIdx.x % C;
     const int rl = threadIdx.x / C;
-    const int64_t S = static_cast<int64_t>(gridDim.x) * rows_per_block;
-    int64_t i = rl < rows_per_block ? static_cast<int64_t>(blockIdx.x) * rows_per_block + rl : n;
-    int64_t e0, e1, f0, f1;  // entry ranges of rows i and i + S
+    const int S = static_cast<int>(gridDim.x) * rows_per_block;
+    int i = rl < rows_per_block ? static_cast<int>(blockIdx.x) * rows_per_block + rl : n;
+    int e0, e1, f0, f1;  // entry ranges of rows i and i + S
     int32_t js[kPipeB];
     XT ws[kPipeB];
     pipe_row_range(row_ptr, i, n, e0, e1);
@@ -223,13 +227,13 @@ csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64
         for (int t = 0; t < kPipeB; ++t)
             if (t < cnt) ldv<XT, V>(xi + static_cast<int64_t>(js[t]) * R + ch * V, xv[t]);
         XT xs[V];
-        ldv<XT, V>(xi + i * R + ch * V, xs);
+        ldv<XT, V>(xi + static_cast<int64_t>(i) * R + ch * V, xs);
         const XT hi = h ? h[i] : XT(0);
         // the next row's first batch and the range of the row after it
         int32_t js2[kPipeB];
         XT ws2[kPipeB];
         pipe_first_batch<kPipeB>(col, val, f0, f1, js2, ws2);
-        int64_t g0, g1;
+        int g0, g1;
         pipe_row_range(row_ptr, i + 2 * S, n, g0, g1);
         XT acc[V];
 #pragma unroll
@@ -242,7 +246,7 @@ csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64
             }
         // entries past the first batch, in entry order
 #pragma unroll 4
-        for (int64_t e = e0 + kPipeB; e < e1; ++e) {
+        for (int e = e0 + kPipeB; e < e1; ++e) {
             const int64_t j = __ldg(col + e);
             const XT w = static_cast<XT>(__ldg(val + e));
             XT xr[V];
@@ -253,7 +257,7 @@ csr_step_pipe_kernel(const XT *__restrict__ xi, XT *__restrict__ xo, const int64
         XT out[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) out[q] = step_update(acc[q] + a * xs[q] + hi, bb, zs, xsc);
-        stv<XT, V>(xo + i * R + ch * V, out);
+        stv<XT, V>(xo + static_cast<int64_t>(i) * R + ch * V, out);
         e0 = f0;
         e1 = f1;
         f0 = g0;
@@ -381,15 +385,18 @@ int step_blocks(const ising_context *c, int C) {
     return static_cast<int>(blocks);
 }
 
-// short rows: the pipelined kernel (one resident wave) serves one instance without the monitor
+// short rows: the pipelined kernel (one resident wave, 32-bit row and entry offsets) serves one
+// instance without the monitor
 bool use_pipe(const ising_context *c, int C, bool traced) {
-    return !traced && c->n_inst == 1 && C <= 256 && c->nnz <= static_cast<int64_t>(kPipeAvgDeg) * c->n;
+    return !traced && c->n_inst == 1 && C <= 256 && c->nnz <= static_cast<int64_t>(kPipeAvgDeg) * c->n &&
+           c->n < (int64_t(1) << 30) && c->nnz < (int64_t(1) << 30);
 }
 
+template <typename XT>
 int pipe_blocks(const ising_context *c, int C) {
     const int rows_per_block = 256 / C;
     int64_t blocks = (c->n + rows_per_block - 1) / rows_per_block;
-    const int64_t cap = static_cast<int64_t>(c->num_sms) * kCsrPipeBlocksPerSm;
+    const int64_t cap = static_cast<int64_t>(c->num_sms) * pipe_blocks_per_sm<XT>();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     return static_cast<int>(blocks);
@@ -410,9 +417,9 @@ void launch_step(const ising_context *c, const XT *xi, XT *xo, int R, const XT *
                  double *hpart, cudaStream_t st) {
     const int C = R / V;
     if (use_pipe(c, C, hpart != nullptr)) {
-        csr_step_pipe_kernel<XT, VT, V><<<static_cast<unsigned>(pipe_blocks(c, C)), 256, 0, st>>>(
-            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, c->n, R, t.alpha, t.alpha_len, k,
-            t.beta, t.zs, t.xsc);
+        csr_step_pipe_kernel<XT, VT, V><<<static_cast<unsigned>(pipe_blocks<XT>(c, C)), 256, 0, st>>>(
+            xi, xo, c->row_ptr, c->col, static_cast<const VT *>(c->val), h, static_cast<int>(c->n), R, t.alpha,
+            t.alpha_len, k, t.beta, t.zs, t.xsc);
         return;
     }
     const int blocks = step_blocks(c, C);
