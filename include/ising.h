@@ -35,7 +35,7 @@
  *  - Threads: one handle must not be used by two threads at once.
  *  - Tuning knobs (environment, read when a handle first needs them):
  *    ISING_LATTICE_PASS = 1, 2 or 3 caps the DOCH steps one pass over a
- *    TORUS2D lattice computes (default 2; every setting gives the same
+ *    TORUS2D lattice computes (default 3; every setting gives the same
  *    iterates bit for bit). ISING_RESIDENT_VARIANT = <threads>:<copies>
  *    (512 or 1024 : 1 or 2) fixes the variant of the shared-memory resident
  *    kernel for batched instances instead of the handle's autotuner (every
@@ -412,13 +412,22 @@ ISING_API ising_status_t ising_energy_torus_noalloc(const int8_t *right, const i
                                                     void *stream);
 
 /*
- * Diagnostic: the FP32 cube root of the stencil kernel, sign(z) 2^(log2|z|/3)
- * evaluated on z 2^(-3k) and rescaled by 2^k, written to ours[i], next to
- * CUDA's cbrtf(z[i]) in ref[i]. z, ours, ref are device arrays of n floats;
- * -40 <= k <= 40. Synchronises the stream.
+ * Diagnostic: the FP32 cube root of the CSR, batched, dense, procedural and
+ * ADOCH kernels, sign(z) 2^(log2|z|/3) evaluated on z 2^(-3k) and rescaled by
+ * 2^k, written to ours[i], next to CUDA's cbrtf(z[i]) in ref[i]. z, ours, ref
+ * are device arrays of n floats; -40 <= k <= 40. Synchronises the stream.
  */
 ISING_API ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
                                              int32_t k, void *stream);
+
+/*
+ * Diagnostic: the FP32 cube root of the lattice DOCH kernels (Eq. FPE's update
+ * cbrt(z / beta)), sign(z) 2^(log2|z|/3 + c3) with c3 = log2(1/beta)/3, one
+ * FMA between the hardware base-2 logarithm and exponential, written to
+ * out[i]. z and out are device arrays of n floats; c3 finite with |c3| <= 64.
+ * Synchronises the stream.
+ */
+ISING_API ising_status_t ising_selftest_cbrt_log(const float *z, float *out, int64_t n, float c3, void *stream);
 
 /*
  * Diagnostic: the procedural couplings J_ij = sin(i j + c) (1-based i, j;

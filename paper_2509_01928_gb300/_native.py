@@ -88,6 +88,8 @@ def load():
     lib.ising_energy_torus_noalloc.restype = ctypes.c_int
     lib.ising_selftest_cbrt.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp]
     lib.ising_selftest_cbrt.restype = ctypes.c_int
+    lib.ising_selftest_cbrt_log.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_float, _vp]
+    lib.ising_selftest_cbrt_log.restype = ctypes.c_int
     lib.ising_selftest_procedural.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int64, _vp, _vp]
     lib.ising_selftest_procedural.restype = ctypes.c_int

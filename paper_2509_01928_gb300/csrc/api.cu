@@ -1204,8 +1204,8 @@ ising_status_t ising_iterate(ising_handle_t h, void *x, int32_t xtype, int32_t R
             const bool pairs_ok = !Hd && c->format == ISING_FMT_TORUS2D && xtype == ISING_F32 &&
                                   !(c->flags & ISING_FLAG_SINGLE_STEP) &&
                                   torus_pair_ok(c, static_cast<const float *>(cur), static_cast<const float *>(nxt), R);
-            // steps per lattice pass: at most 2 (default) or ISING_LATTICE_PASS = 1, 2 or 3
-            int per_pass = 2;
+            // steps per lattice pass: at most 3 (default) or ISING_LATTICE_PASS = 1, 2 or 3
+            int per_pass = 3;
             if (const char *env = std::getenv("ISING_LATTICE_PASS")) {
                 const int v = std::atoi(env);
                 if (v >= 1 && v <= 3) per_pass = v;

@@ -1,4 +1,5 @@
-// Real (odd) cube root used by the FP32 stencil kernel.
+// Real (odd) cube roots of the FP32 kernels: cbrt_pow2 (CSR, batched, dense,
+// procedural and ADOCH kernels) and cbrt_log (the lattice DOCH kernels).
 //
 // cbrt(z) = sign(z) * 2^(log2|z| / 3), with the hardware approximations of
 // the base-2 logarithm and exponential (PTX lg2.approx.ftz.f32 and
@@ -17,6 +18,23 @@ __device__ __forceinline__ float cbrt_pow2(float z) {
     float l, y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(fabsf(z)));
     l *= (1.0f / 3.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+    return copysignf(y, z);
+}
+
+// cbrt(z / beta) as sign(z) 2^(log2|z| / 3 + c3) with c3 = -log2(beta) / 3 given:
+// one FMA joins the division by three and the scale, and no products by the
+// power-of-two prescale are needed (two instructions fewer than cbrt_pow2 with
+// its scales). The FP32 value l = log2|z| / 3 + c3 carries an absolute rounding
+// of (|log2 z| / 3 + |l|) 2^-24, which exp2 turns into a relative error of at
+// most ln 2 times that; with the hardware log2/exp2 approximations the error is
+// within 2^-21 + (0.25 |log2 z| + 0.75 |l|) 2^-24. In the lattice iteration |l|
+// and |log2 z| stay near the attractor scale. z = 0 and subnormal z give 0.
+// Tested against cbrt through ising_selftest_cbrt_log.
+__device__ __forceinline__ float cbrt_log(float z, float c3) {
+    float l, y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(fabsf(z)));
+    l = fmaf(l, 1.0f / 3.0f, c3);
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
     return copysignf(y, z);
 }

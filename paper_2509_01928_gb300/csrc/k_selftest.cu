@@ -1,5 +1,8 @@
-// Diagnostic entry point: the device cube root of the stencil kernel next to
-// CUDA's cbrtf on the same inputs (see ising_selftest_cbrt in ising.h).
+// Diagnostic entry points: the device cube root cbrt_pow2 next to
+// CUDA's cbrtf on the same inputs (see ising_selftest_cbrt in ising.h), and the
+// lattice kernels' cube root with its log-domain offset (ising_selftest_cbrt_log).
+#include <cmath>
+
 #include "cbrt.cuh"
 #include "internal.cuh"
 
@@ -15,8 +18,32 @@ __global__ void cbrt_pair(const float *__restrict__ z, float *__restrict__ ours,
     }
 }
 
+__global__ void cbrt_log_kernel(const float *__restrict__ z, float *__restrict__ out, int64_t n, float c3) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = cbrt_log(z[i], c3);
+}
+
 }  // namespace
 }  // namespace doch
+
+extern "C" ising_status_t ising_selftest_cbrt_log(const float *z, float *out, int64_t n, float c3, void *stream) {
+    return doch::guarded([&]() -> ising_status_t {
+        using namespace doch;
+        if (!z || !out || n < 0 || !std::isfinite(c3) || std::fabs(c3) > 64.f)
+            return fail(ISING_ERR_INVALID_ARG, "selftest_cbrt_log: bad argument");
+        if (n == 0) return ISING_OK;
+        int dev = 0, sms = 1;
+        DOCH_CUDA(cudaGetDevice(&dev));
+        DOCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms) blocks = 8LL * sms;
+        cbrt_log_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, out, n, c3);
+        DOCH_CUDA(cudaGetLastError());
+        DOCH_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        return ISING_OK;
+    });
+}
 
 extern "C" ising_status_t ising_selftest_cbrt(const float *z, float *ours, float *ref, int64_t n,
                                               int32_t k, void *stream) {

@@ -16,11 +16,11 @@
 // column 0. Per site and step the kernel reads x once (4 B), both couplings
 // once (2 B) and writes x once (4 B), plus 2 extra x rows per strip.
 //
-// Cube root: cbrt(z) = 2^(k) * exp2( log2(|z| 2^(-3k)) / 3 ) with sign, using
-// the hardware base-2 logarithm/exponential approximations (PTX lg2.approx,
-// ex2.approx). The exact power-of-two prescale 2^(-3k) is folded into 1/beta
-// (k chosen on the host from beta) so |log2| stays small and the FP32 log
-// keeps its precision; relative error ~2^-22.
+// Cube root: cbrt(z / beta) = sign(z) exp2( log2|z| / 3 + c3 ), c3 = log2(1/beta) / 3
+// from the host, with the hardware base-2 logarithm/exponential approximations
+// (PTX lg2.approx, ex2.approx): cbrt_log of cbrt.cuh, one FMA between the two
+// (relative error within 2^-21 + (0.25 |log2 z| + 0.75 |l|) 2^-24, l the
+// exponent; near the attractor both logarithms are small).
 #include <cmath>
 
 #include "cbrt.cuh"
@@ -56,8 +56,8 @@ __device__ __forceinline__ float site_sum(float wr, float xr, float wl, float xl
     return wr * xr + wl * xl + wd * xd + wu * xu;
 }
 
-__device__ __forceinline__ float site_new(float u, float x, float alpha, float zscale, float xscale) {
-    return cbrt_pow2((u + alpha * x) * zscale) * xscale;
+__device__ __forceinline__ float site_new(float u, float x, float alpha, float c3) {
+    return cbrt_log(u + alpha * x, c3);
 }
 
 // four consecutive sites c..c+3 of one row: xm row values, xl/xr the values
@@ -66,13 +66,13 @@ __device__ __forceinline__ float site_new(float u, float x, float alpha, float z
 // couplings of this row / of the row above (as floats)
 __device__ __forceinline__ float4 row4_new_w(float4 xm, float xl, float xr, float4 xu, float4 xd,
                                              const float (&wr)[4], float wleft, const float (&dd)[4],
-                                             const float (&du)[4], float alpha, float zscale, float xscale) {
+                                             const float (&du)[4], float alpha, float c3) {
     const float w0 = wr[0], w1 = wr[1], w2 = wr[2], w3 = wr[3];
     float4 out;
-    out.x = site_new(site_sum(w0, xm.y, wleft, xl, dd[0], xd.x, du[0], xu.x), xm.x, alpha, zscale, xscale);
-    out.y = site_new(site_sum(w1, xm.z, w0, xm.x, dd[1], xd.y, du[1], xu.y), xm.y, alpha, zscale, xscale);
-    out.z = site_new(site_sum(w2, xm.w, w1, xm.y, dd[2], xd.z, du[2], xu.z), xm.z, alpha, zscale, xscale);
-    out.w = site_new(site_sum(w3, xr, w2, xm.z, dd[3], xd.w, du[3], xu.w), xm.w, alpha, zscale, xscale);
+    out.x = site_new(site_sum(w0, xm.y, wleft, xl, dd[0], xd.x, du[0], xu.x), xm.x, alpha, c3);
+    out.y = site_new(site_sum(w1, xm.z, w0, xm.x, dd[1], xd.y, du[1], xu.y), xm.y, alpha, c3);
+    out.z = site_new(site_sum(w2, xm.w, w1, xm.y, dd[2], xd.z, du[2], xu.z), xm.z, alpha, c3);
+    out.w = site_new(site_sum(w3, xr, w2, xm.z, dd[3], xd.w, du[3], xu.w), xm.w, alpha, c3);
     return out;
 }
 
@@ -87,10 +87,10 @@ __device__ __forceinline__ void unpack4_cvt(int v, float (&f)[4]) {
 
 __device__ __forceinline__ float4 row4_new(float4 xm, float xl, float xr, float4 xu, float4 xd, int rt,
                                            float wleft, const float (&dd)[4], const float (&du)[4], float alpha,
-                                           float zscale, float xscale) {
+                                           float c3) {
     float wr[4];
     unpack4_cvt(rt, wr);
-    return row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha, zscale, xscale);
+    return row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha, c3);
 }
 
 // u of four consecutive sites (the sums row4_new_w feeds to site_new)
@@ -132,7 +132,7 @@ template <bool TRACE>
 __global__ void __launch_bounds__(kThreads, TRACE ? 4 : 6)
 torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
                   const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
-                  int tiles, int bpt, float alpha, float zscale, float xscale, double *__restrict__ hpart) {
+                  int tiles, int bpt, float alpha, float c3, double *__restrict__ hpart) {
     const int tile = blockIdx.x % tiles;
     const int part = blockIdx.x / tiles;
     const int r0 = static_cast<int>(static_cast<int64_t>(Lr) * part / bpt);
@@ -203,10 +203,10 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
             unpack4_cvt(rt, wr);
             const float4 u = row4_u(xm, xl, xr, xu, xd, wr, wleft, dd, du);
             float4 out;
-            out.x = site_new(u.x, xm.x, alpha, zscale, xscale);
-            out.y = site_new(u.y, xm.y, alpha, zscale, xscale);
-            out.z = site_new(u.z, xm.z, alpha, zscale, xscale);
-            out.w = site_new(u.w, xm.w, alpha, zscale, xscale);
+            out.x = site_new(u.x, xm.x, alpha, c3);
+            out.y = site_new(u.y, xm.y, alpha, c3);
+            out.z = site_new(u.z, xm.z, alpha, c3);
+            out.w = site_new(u.w, xm.w, alpha, c3);
             if (active) {
                 __stcs(reinterpret_cast<float4 *>(oc + o), out);
                 const float xv[4] = {xm.x, xm.y, xm.z, xm.w}, uv[4] = {u.x, u.y, u.z, u.w};
@@ -219,7 +219,7 @@ torus_f32_r1_vec4(const float *__restrict__ xi, float *__restrict__ xo,
                 }
             }
         } else {
-            const float4 out = row4_new(xm, xl, xr, xu, xd, rt, wleft, dd, du, alpha, zscale, xscale);
+            const float4 out = row4_new(xm, xl, xr, xu, xd, rt, wleft, dd, du, alpha, c3);
             if (active) __stcs(reinterpret_cast<float4 *>(oc + o), out);
         }
 
@@ -279,7 +279,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, 3)
 torus_f32_r1_vec4_t2(const float *__restrict__ xi, float *__restrict__ xo,
                      const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
-                     int segs, int bpt, float alpha1, float alpha2, float zscale, float xscale) {
+                     int segs, int bpt, float alpha1, float alpha2, float c3) {
     extern __shared__ __align__(16) unsigned char t2_smem[];
     T2Ring<D> &ring = *reinterpret_cast<T2Ring<D> *>(t2_smem);
     const int t = threadIdx.x;
@@ -356,14 +356,14 @@ torus_f32_r1_vec4_t2(const float *__restrict__ xi, float *__restrict__ xo,
         const float xl = __shfl_up_sync(kFull, xm.w, 1);
         const float xr = __shfl_down_sync(kFull, xm.x, 1);
         const float wleft = __shfl_up_sync(kFull, wr[3], 1);
-        const float4 yc = row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha1, zscale, xscale);
+        const float4 yc = row4_new_w(xm, xl, xr, xu, xd, wr, wleft, dd, du, alpha1, c3);
 
         // ---- step 2: z row r-1 from y rows r-2, r-1, r (once y row r0-1 is two rows back)
         if (i > 1) {
             const float yl = __shfl_up_sync(kFull, yb.w, 1);
             const float yr = __shfl_down_sync(kFull, yb.x, 1);
             const float wleftp = __shfl_up_sync(kFull, wr_p[3], 1);
-            const float4 z = row4_new_w(yb, yl, yr, ya, yc, wr_p, wleftp, du, du_p, alpha2, zscale, xscale);
+            const float4 z = row4_new_w(yb, yl, yr, ya, yc, wr_p, wleftp, du, du_p, alpha2, c3);
             if (writes) __stcs(reinterpret_cast<float4 *>(xo + c + os), z);
             os = wrap_dn(os);
         }
@@ -393,7 +393,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, 2)
 torus_f32_r1_vec4_t3(const float *__restrict__ xi, float *__restrict__ xo,
                      const int8_t *__restrict__ right, const int8_t *__restrict__ down, int Lr, int Lc,
-                     int segs, int bpt, float alpha1, float alpha2, float alpha3, float zscale, float xscale) {
+                     int segs, int bpt, float alpha1, float alpha2, float alpha3, float c3) {
     extern __shared__ __align__(16) unsigned char t3_smem[];
     T2Ring<D> &ring = *reinterpret_cast<T2Ring<D> *>(t3_smem);
     const int t = threadIdx.x;
@@ -462,7 +462,7 @@ torus_f32_r1_vec4_t3(const float *__restrict__ xi, float *__restrict__ xo,
         const float xl = __shfl_up_sync(kFull, xm.w, 1);
         const float xr = __shfl_down_sync(kFull, xm.x, 1);
         const float wl0 = __shfl_up_sync(kFull, w0[3], 1);
-        const float4 y1 = row4_new_w(xm, xl, xr, xu, xd, w0, wl0, d0, d1, alpha1, zscale, xscale);
+        const float4 y1 = row4_new_w(xm, xl, xr, xu, xd, w0, wl0, d0, d1, alpha1, c3);
 
         // ---- level 2: row r-1 from level-1 rows r-2, r-1, r
         float4 y2 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -470,14 +470,14 @@ torus_f32_r1_vec4_t3(const float *__restrict__ xi, float *__restrict__ xo,
             const float yl = __shfl_up_sync(kFull, yb1.w, 1);
             const float yr = __shfl_down_sync(kFull, yb1.x, 1);
             const float wl1 = __shfl_up_sync(kFull, w1[3], 1);
-            y2 = row4_new_w(yb1, yl, yr, ya1, y1, w1, wl1, d1, d2, alpha2, zscale, xscale);
+            y2 = row4_new_w(yb1, yl, yr, ya1, y1, w1, wl1, d1, d2, alpha2, c3);
         }
         // ---- level 3: row r-2 from level-2 rows r-3, r-2, r-1, written out
         if (i >= 4) {
             const float zl = __shfl_up_sync(kFull, yb2.w, 1);
             const float zr = __shfl_down_sync(kFull, yb2.x, 1);
             const float wl2 = __shfl_up_sync(kFull, w2[3], 1);
-            const float4 z = row4_new_w(yb2, zl, zr, ya2, y2, w2, wl2, d2, d3, alpha3, zscale, xscale);
+            const float4 z = row4_new_w(yb2, zl, zr, ya2, y2, w2, wl2, d2, d3, alpha3, c3);
             if (writes) __stcs(reinterpret_cast<float4 *>(xo + c + os), z);
             os = wrap_dn(os);
         }
@@ -589,17 +589,18 @@ bool vec4_ok(const ising_context *c, const float *x_in, const float *x_out, int 
 
 }  // namespace
 
+// the lattice cube root's offset c3 = log2(1 / beta) / 3 (cbrt_log)
+static float lattice_c3(double inv_beta) { return static_cast<float>(std::log2(inv_beta) / 3.0); }
+
 ising_status_t torus_step_f32_traced(ising_context *c, const float *x_in, float *x_out, int R, float alpha,
                                      double inv_beta, double alpha_k, double beta, double *H_out, cudaStream_t st) {
     if (!vec4_ok(c, x_in, x_out, R)) return ISING_ERR_UNSUPPORTED;
     const Vec4Shape v = vec4_shape(c);
     DOCH_CHECK(c->partials.ensure(sizeof(double) * 4 * static_cast<size_t>(v.blocks())));
-    const int k = cbrt_prescale_exp(inv_beta);
-    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
-    const float xscale = std::ldexp(1.0f, -k);
+    const float c3 = lattice_c3(inv_beta);
     torus_f32_r1_vec4<true><<<static_cast<unsigned>(v.blocks()), kThreads, 0, st>>>(
         x_in, x_out, c->right, c->down, static_cast<int>(c->l_rows), static_cast<int>(c->l_cols), v.tiles,
-        static_cast<int>(v.bpt), alpha, zscale, xscale, c->partials.as<double>());
+        static_cast<int>(v.bpt), alpha, c3, c->partials.as<double>());
     DOCH_CUDA(cudaGetLastError());
     return ham_fused_finish_launch(c->partials.as<double>(), static_cast<int>(v.blocks()), 1, alpha_k, beta, H_out, st);
 }
@@ -609,12 +610,10 @@ ising_status_t torus_step_f32(const ising_context *c, const float *x_in, float *
     const int64_t Lr = c->l_rows, Lc = c->l_cols;
     if (vec4_ok(c, x_in, x_out, R)) {
         const Vec4Shape v = vec4_shape(c);
-        const int k = cbrt_prescale_exp(inv_beta);
-        const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
-        const float xscale = std::ldexp(1.0f, -k);
+        const float c3 = lattice_c3(inv_beta);
         torus_f32_r1_vec4<false><<<static_cast<unsigned>(v.blocks()), kThreads, 0, st>>>(
             x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), v.tiles,
-            static_cast<int>(v.bpt), alpha, zscale, xscale, nullptr);
+            static_cast<int>(v.bpt), alpha, c3, nullptr);
     } else {
         const int64_t total = Lr * Lc * R;
         int64_t blocks = (total + 255) / 256;
@@ -647,12 +646,10 @@ ising_status_t torus_pair_f32(const ising_context *c, const float *x_in, float *
     const int64_t warps = segs * bpt;
     const int64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
     if (blocks > INT32_MAX || segs > INT32_MAX) return fail(ISING_ERR_UNSUPPORTED, "lattice too large");
-    const int k = cbrt_prescale_exp(inv_beta);
-    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
-    const float xscale = std::ldexp(1.0f, -k);
+    const float c3 = lattice_c3(inv_beta);
     torus_f32_r1_vec4_t2<kT2Depth><<<static_cast<unsigned>(blocks), kThreads, kT2Smem, st>>>(
         x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), static_cast<int>(segs),
-        static_cast<int>(bpt), alpha1, alpha2, zscale, xscale);
+        static_cast<int>(bpt), alpha1, alpha2, c3);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }
@@ -669,12 +666,10 @@ ising_status_t torus_triple_f32(const ising_context *c, const float *x_in, float
     const int64_t warps = segs * bpt;
     const int64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
     if (blocks > INT32_MAX || segs > INT32_MAX) return fail(ISING_ERR_UNSUPPORTED, "lattice too large");
-    const int k = cbrt_prescale_exp(inv_beta);
-    const float zscale = static_cast<float>(std::ldexp(inv_beta, 3 * k));
-    const float xscale = std::ldexp(1.0f, -k);
+    const float c3 = lattice_c3(inv_beta);
     torus_f32_r1_vec4_t3<kT2Depth><<<static_cast<unsigned>(blocks), kThreads, kT2Smem, st>>>(
         x_in, x_out, c->right, c->down, static_cast<int>(Lr), static_cast<int>(Lc), static_cast<int>(segs),
-        static_cast<int>(bpt), alpha1, alpha2, alpha3, zscale, xscale);
+        static_cast<int>(bpt), alpha1, alpha2, alpha3, c3);
     DOCH_CUDA(cudaGetLastError());
     return ISING_OK;
 }

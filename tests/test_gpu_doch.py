@@ -442,6 +442,38 @@ def test_stencil_cube_root_accuracy(k):
     assert np.all(o[-4:] == 0.0)
 
 
+@pytest.mark.parametrize("c3", [-7.3, -1.1, 0.0, 0.5, 3.7])
+def test_lattice_cube_root_accuracy(c3):
+    """Relative error of the lattice kernels' cube root sign(z) 2^(log2|z|/3 + c3) (cbrt_log)
+    against the FP64 value cbrt(z) 2^c3, for |z| in [2^-60, 2^60]; odd; 0 -> 0.
+
+    Bound derived from the arithmetic: the FP32 value L = log2|z| carries an absolute rounding
+    of |L| 2^-24, and l = L/3 + c3 (one FMA) one of |l| 2^-24; exp2 turns an absolute error e
+    of l into a relative error of ln 2 e, so the two give at most (ln 2 / 3 |L| + ln 2 |l|) 2^-24
+    < (0.25 |L| + 0.75 |l|) 2^-24; the hardware log2/exp2 approximations add about 2^-21."""
+    u = I.uniform01(I.stream_seed(19, int(10 * c3) + 100), 0, 1 << 20)
+    e = -60.0 + 120.0 * u
+    sg = I.signs(I.stream_seed(19, int(10 * c3) + 200), 0, 1 << 20)
+    z = (sg * np.exp2(e)).astype(np.float32)
+    z = np.concatenate([z, -z[:1000], np.zeros(4, np.float32)])
+    zd = _dev(z)
+    out = torch.empty_like(zd)
+    st = N.load().ising_selftest_cbrt_log(N._ptr(zd), N._ptr(out), z.size, float(np.float32(c3)), None)
+    assert st == 0
+    o = out.cpu().numpy().astype(np.float64)
+    z64 = z.astype(np.float64)
+    c3f = float(np.float32(c3))
+    ref = np.cbrt(z64) * 2.0 ** c3f
+    nz = z64 != 0
+    rel = np.abs(o[nz] - ref[nz]) / np.abs(ref[nz])
+    L = np.log2(np.abs(z64[nz]))
+    l = L / 3.0 + c3f
+    bound = 2.0 ** -21 + (0.25 * np.abs(L) + 0.75 * np.abs(l)) * 2.0 ** -24
+    assert np.all(rel <= bound), (rel / bound).max()
+    assert np.array_equal(np.sign(o), np.sign(z64))
+    assert np.all(o[-4:] == 0.0)
+
+
 def test_ell_input_runs_as_csr():
     """ELL rows (empty slots -1) create the CSR problem: the iterates of the two handles agree
     bit for bit (FP32 and FP64)."""
